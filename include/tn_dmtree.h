@@ -1,0 +1,187 @@
+/*
+ * tn_dmtree.h -- C ABI of the GB300 density-matrix tree-approximation library.
+ *
+ * The library approximately contracts a closed tensor network with the
+ * partitioned_contract algorithm (Sec. 3.2, Algorithm partitioned_contract):
+ * partitions are absorbed one at a time along a linear path; each absorption
+ * embeds the intermediate network into a low-rank MPS-shaped binary tree with
+ * the density-matrix algorithm (Sec. 5, Algorithm density_matrix_alg, with the
+ * memoised density matrices of Eq. dm_cache), and the last absorption closes
+ * the network into the scalar Z.  All tensor arithmetic runs in the library's
+ * own sm_103a CUDA kernels; there is no CPU fallback.
+ *
+ * Conventions (every entry point):
+ *   - Dense tensors are row-major, last leg fastest.  A site tensor holds one
+ *     leg per incident edge, in ascending edge-id order.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory of the ctx's device.  Pointer arrays themselves (T* const*)
+ *     are always host arrays.
+ *   - Inputs are owned by the caller and are not retained after a call
+ *     returns, except that a batch launched by tn_contract_approx reads its
+ *     plans and device inputs until tn_logz returns.
+ *   - The ctx owns all device workspace; it grows on demand and is freed by
+ *     tn_ctx_destroy.  One ctx must not be used by two host threads at once.
+ *   - No C++ exception crosses the ABI.  Every call returns a tn_status;
+ *     tn_last_error() gives a one-line reason for the last non-OK status.
+ */
+#ifndef TN_DMTREE_H
+#define TN_DMTREE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TN_OK = 0,
+  TN_ERR_INVALID = 1,      /* malformed graph, partition, path or argument      */
+  TN_ERR_OOM = 2,          /* device or host allocation failed                  */
+  TN_ERR_CUDA = 3,         /* a CUDA runtime call failed                        */
+  TN_ERR_NONFINITE = 4,    /* NaN/Inf met in an instance (per-instance status)  */
+  TN_ERR_NONPOSITIVE = 5,  /* final scalar <= 0, ln Z undefined (per instance)  */
+  TN_ERR_TIMEOUT = 6,      /* a bounded device wait expired                     */
+  TN_ERR_EIG_NOCONV = 7,   /* eigensolver hit its iteration cap                 */
+  TN_ERR_UNSUPPORTED = 8   /* valid input outside what this build implements    */
+} tn_status;
+
+/* Arithmetic of the hot path.
+ *   TN_PREC_FP64: every contraction, eigensolver and scale in FP64.
+ *   TN_PREC_TF32: density-matrix contractions on tcgen05 tensor cores with
+ *                 TF32 inputs and FP32 accumulation; the value path (local
+ *                 block, projector, root) with a 3-term TF32 split
+ *                 (compensated); eigensolver reduction in FP32 with FP64
+ *                 eigenvalue refinement; log-scale in FP64.
+ *   TN_PREC_BF16: as TF32 but BF16 operands (3-term BF16 split on the value
+ *                 path).                                                     */
+enum { TN_PREC_FP64 = 0, TN_PREC_BF16 = 1, TN_PREC_TF32 = 2 };
+
+/* The tensor network graph G = (V, E) of Sec. 2.1.  Host memory, caller-owned.
+ * edge_v[e] == -1 marks an open (uncontracted) edge; this build requires a
+ * closed network (no open edges) because it returns ln Z.                  */
+typedef struct {
+  int32_t n_vertices;
+  int32_t n_edges;
+  const int32_t* edge_u;    /* [n_edges] endpoint vertex ids                 */
+  const int32_t* edge_v;    /* [n_edges] other endpoint, or -1 (open)        */
+  const int32_t* edge_dim;  /* [n_edges] mode size s, w(e) = ln s (Sec. 2.1) */
+} tn_graph;
+
+/* Inputs of Algorithm partitioned_contract (Sec. 3.2): the partition V_i, the
+ * contraction path over it, the ansatz, the maximum bond size chi and the swap
+ * batch size r.  Host memory, caller-owned.                                  */
+typedef struct {
+  int32_t chi_max;          /* maximum bond size chi (>= 1)                    */
+  int32_t env_size;         /* vertices per partition when partition == NULL:
+                               part i = vertices [i*env_size, (i+1)*env_size) */
+  const int32_t* partition; /* [n_vertices] part id in 0..N-1, or NULL       */
+  const int32_t* path;      /* [n_path] order in which parts are absorbed
+                               (maximally unbalanced path), or NULL = 0..N-1  */
+  int32_t n_path;
+  int32_t ansatz;           /* 0 = MPS embedding tree (App. C); others: UNSUPPORTED */
+  int32_t swap_batch;       /* swap batch size r of Algorithm approx_tensor_network */
+} tn_plan_opts;
+
+typedef struct tn_plan tn_plan_t;
+typedef struct tn_ctx tn_ctx_t;
+
+/* Summary of a plan (host).  Flop counts use the cost model of Sec. 2.2
+ * (2 flops per multiply-add) over the contractions the plan will execute. */
+typedef struct {
+  int32_t n_steps;          /* contractions on the path (= parts - 1)          */
+  int32_t n_dm_passes;      /* density_matrix_alg passes                       */
+  int32_t max_legs;         /* most open legs of any intermediate              */
+  int32_t max_bond;         /* largest untruncated tree-edge dimension         */
+  int32_t max_eig_n;        /* largest density matrix order                    */
+  int64_t site_elems;       /* doubles in one instance's packed site buffer    */
+  double flops_env;         /* root-side memo density matrices (Eq. dm_cache)  */
+  double flops_local;       /* local blocks M_v                                */
+  double flops_density;     /* density matrices L_v = M_v L_u M_v^T            */
+  double flops_project;     /* projector application U_v^T M_v and the root    */
+  double flops_eig;         /* eigensolver (Householder + back-transform)      */
+  int64_t n_eig;            /* eigensolves per instance                        */
+} tn_plan_info;
+
+/* ---------------------------------------------------------------- planning
+ * Build the host-side plan of Algorithm partitioned_contract for one graph:
+ * partitions, the linear path, the edge ordering of every intermediate
+ * (Sec. 4), the MPS embedding tree of each step (App. C) and the embedding
+ * phi of its tensors (Algorithm tree_embedding), down to a flat list of
+ * contraction / eigensolve / projection ops with their shapes.  Depends only
+ * on the graph, never on tensor data (Sec. 3.2).  Host only; no CUDA call.
+ * Supported: every part is a simple path of vertices whose i-th vertex
+ * absorbs the i-th open leg of the intermediate and emits at most one new
+ * open leg (boundary absorption as in the 2D lattice workloads).  Anything
+ * else returns TN_ERR_UNSUPPORTED with a reason.
+ * Returns TN_ERR_INVALID for malformed input.  *out is owned by the caller
+ * and released with tn_plan_destroy.                                         */
+tn_status tn_plan(const tn_graph* graph, const tn_plan_opts* opts, tn_plan_t** out);
+tn_status tn_plan_destroy(tn_plan_t* plan);
+tn_status tn_plan_query(const tn_plan_t* plan, tn_plan_info* info);
+/* Offset (in doubles) of vertex v's tensor inside a packed site buffer.    */
+tn_status tn_plan_site_offset(const tn_plan_t* plan, int32_t vertex, int64_t* offset);
+
+/* ------------------------------------------------------------------- context
+ * A ctx binds one CUDA device and owns the device workspace.  device is a
+ * CUDA ordinal.  Fails with TN_ERR_CUDA if the device cannot be used.       */
+tn_status tn_ctx_create(int32_t device, tn_ctx_t** out);
+tn_status tn_ctx_destroy(tn_ctx_t* ctx);
+
+/* --------------------------------------------------------- one DM pass
+ * Algorithm density_matrix_alg (Sec. 5) on an MPS embedding tree with n leaves,
+ * for n_inst independent instances of identical shape.  The intermediate
+ * network is given with the tensors of each tree vertex already contracted
+ * ("contract T(v) first", Sec. 5.3): blocks Y_0..Y_{n-1} of shapes
+ *   Y_0: (1, d_0, D_0),  Y_k: (D_{k-1}, d_k, D_k),  Y_{n-1}: (D_{n-2}, d_{n-1}, 1)
+ * packed back to back in blocks_dev[i] (device, FP64).  Tree vertex 1 joins
+ * leaves x_0 and x_1 (App. C, Def. MPS tree).
+ * Ranks: r_k = min(chi_k, r_{k-1} d_k, D_k, prod_{j>k} d_j) with r_0 = d_0 and
+ * chi_k = chi_per_edge ? chi_per_edge[k] : chi (k = 1..n-2).
+ * Output (device, FP64, caller-allocated, tree_dev[i] per instance): the tree
+ * tensors packed back to back: U_1 (d_0, d_1, r_1), U_k (r_{k-1}, d_k, r_k)
+ * for k = 2..n-2, then the unit-Frobenius-norm root M_r (r_{n-2}, d_{n-1}).
+ * Every U_k has orthonormal columns (as a (r_{k-1} d_k) x r_k matrix); each
+ * column is signed so that its largest-|.| entry is positive.
+ * lognorm_dev[i] (device) receives ln ||M_r|| before scaling; status_dev[i]
+ * (device) a tn_status per instance.  ranks_host (host, n-1 entries) receives
+ * r_0..r_{n-2}.  Asynchronous on stream (a cudaStream_t, NULL = default).  */
+tn_status tn_embed_tree(tn_ctx_t* ctx, int32_t n_inst, int32_t n_legs,
+                        const int32_t* leg_dim, const int32_t* bond_dim,
+                        const double* const* blocks_dev, int32_t chi,
+                        const int32_t* chi_per_edge, int32_t precision,
+                        double* const* tree_dev, double* lognorm_dev,
+                        int32_t* status_dev, int32_t* ranks_host, void* stream);
+
+/* ------------------------------------------------------- whole contraction
+ * Algorithm partitioned_contract for a batch of n_inst instances.  plans[i]
+ * must be structurally identical (same graph shape, partition, path and
+ * chi); instances differ in tensor data only.  sites_dev[i] is a device FP64
+ * buffer with every site tensor of instance i packed at tn_plan_site_offset.
+ * Asynchronous on stream; results are read with tn_logz.  learned_chi must
+ * be 0 in this build.                                                       */
+tn_status tn_contract_approx(tn_ctx_t* ctx, const tn_plan_t* const* plans, int32_t n_inst,
+                             const double* const* sites_dev, int32_t precision,
+                             int32_t learned_chi, void* stream);
+
+/* Waits for the last tn_contract_approx of ctx and copies its results to the
+ * host: logz_host[i] = ln Z of instance i (NaN if status != TN_OK) and
+ * status_host[i] its tn_status.  Returns the first non-OK instance status.  */
+tn_status tn_logz(tn_ctx_t* ctx, double* logz_host, int32_t* status_host, int32_t n_inst);
+
+/* End-to-end form of tn_contract_approx + tn_logz from HOST site buffers:
+ * copies sites_host[i] (host, FP64, packed as above; page-locked memory gives
+ * asynchronous copies) to ctx-owned device memory, runs the batch and copies
+ * ln Z and statuses back.  Synchronous.                                      */
+tn_status tn_contract_approx_host(tn_ctx_t* ctx, const tn_plan_t* const* plans, int32_t n_inst,
+                                  const double* const* sites_host, int32_t precision,
+                                  int32_t learned_chi, double* logz_host,
+                                  int32_t* status_host, void* stream);
+
+/* One-line reason for the last non-OK status returned on this thread (ctx
+ * may be NULL for calls that have none).  Valid until the next call.       */
+const char* tn_last_error(const tn_ctx_t* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TN_DMTREE_H */

@@ -124,7 +124,8 @@ def density_matrix_alg(blocks, chi, trace=None, force_branch=None):
     for v in range(n - 2, 0, -1):
         Bk = blocks[v + 1]                           # (D_v, d_{v+1}, D_{v+1})
         env = dm_parent[v + 1]                       # dm(v+2, v+1): (D_{v+1}, D_{v+1})
-        L = np.einsum("aeb,bc,fec->af", Bk, env, Bk)
+        # the identity on leaf x_{v+1} in the Kronecker product = a sum over it
+        L = sum(Bk[:, e, :] @ env @ Bk[:, e, :].T for e in range(Bk.shape[1]))
         dm_parent[v] = L / np.max(np.abs(L))
     # Post-order traversal of the MPS tree: vertices 1, 2, ..., n-2, then root.
     U = [None] * n
@@ -135,7 +136,7 @@ def density_matrix_alg(blocks, chi, trace=None, force_branch=None):
         if v == 1:
             M = blocks[1].reshape(d[0] * d[1], -1)
         else:
-            M = np.einsum("ia,aeb->ieb", P, blocks[v]).reshape(P.shape[0] * d[v], -1)
+            M = np.tensordot(P, blocks[v], axes=(1, 0)).reshape(P.shape[0] * d[v], -1)
         dimA, dimB = M.shape
         beyond = int(np.prod(d[v + 1:]))             # open legs on the parent side
         r = min(chi, dimA, dimB, beyond)
@@ -164,7 +165,7 @@ def density_matrix_alg(blocks, chi, trace=None, force_branch=None):
         # Fold T'(v) and U_v^T into the parent: the parent now sees P = U_v^T M_v.
         P = Uv.T @ M
     # Root: M_r = contraction of T'(root).
-    Mr = np.einsum("ia,aeb->ieb", P, blocks[n - 1]).reshape(P.shape[0], d[n - 1])
+    Mr = np.tensordot(P, blocks[n - 1], axes=(1, 0)).reshape(P.shape[0], d[n - 1])
     nrm = np.linalg.norm(Mr)
     return U, Mr / nrm, float(np.log(nrm))
 

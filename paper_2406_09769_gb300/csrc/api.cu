@@ -1,0 +1,607 @@
+// C ABI entry points: device context, workspace, and the executor that runs a
+// plan of Algorithm partitioned_contract on the GPU for a batch of instances.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "tn_internal.h"
+
+namespace {
+
+struct Fail {
+  tn_status st;
+  std::string msg;
+};
+
+[[noreturn]] void fail(tn_status st, const std::string& msg) { throw Fail{st, msg}; }
+
+void ck(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) fail(TN_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Host-side allocation fault injection: TN_FAULT_ALLOC_AT=n makes the n-th
+// device allocation of the process fail with TN_ERR_OOM (no CUDA call made).
+long g_alloc_count = 0;
+bool inject_alloc_failure() {
+  static long at = [] {
+    const char* s = std::getenv("TN_FAULT_ALLOC_AT");
+    return s ? std::atol(s) : 0L;
+  }();
+  ++g_alloc_count;
+  return at > 0 && g_alloc_count == at;
+}
+
+// A device buffer that only grows.
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  void* get(size_t bytes) {
+    if (bytes <= cap) return p;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    if (inject_alloc_failure()) fail(TN_ERR_OOM, "device allocation failed (injected)");
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      fail(TN_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    }
+    cap = bytes;
+    return p;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+}  // namespace
+
+struct tn_ctx {
+  int device = 0;
+  std::string err;
+  cudaStream_t stream = nullptr;
+  int last_batch = 0;
+  bool pending = false;
+  // workspace
+  DevBuf arena, stage, tables, results;
+  void* pinned = nullptr;
+  size_t pinned_cap = 0;
+  cudaEvent_t pinned_free = nullptr;
+  // device pointers carved from `results`
+  double* logz = nullptr;
+  int* status = nullptr;
+  double* logscale = nullptr;
+};
+
+namespace {
+
+struct Ws {
+  // per-instance strides (elements) and base pointers
+  long long sS, sY, sR, sX, sM, sL, sP, sLam, sAmax, sInv;
+  double *S0, *S1, *Y, *R, *X, *M, *G, *L, *P, *lam, *inv;
+  unsigned long long* amax;
+};
+
+struct Dims {
+  long long maxS = 1, maxY = 1, maxR = 1, maxX = 1, maxM = 1, maxL = 1, maxP = 1, maxLam = 1;
+  int maxN = 1, maxD = 1;
+};
+
+Dims plan_dims(const tn_plan_t* P) {
+  Dims d;
+  for (const tn::Step& st : P->steps) {
+    d.maxS = std::max<long long>(d.maxS, st.s_total);
+    d.maxY = std::max<long long>(d.maxY, st.y_total);
+    d.maxR = std::max<long long>(d.maxR, st.r_total);
+    d.maxN = std::max(d.maxN, st.n);
+    for (int k = 0; k < st.n; ++k) {
+      d.maxD = std::max(d.maxD, st.D[k]);
+      const tn::SiteOp& o = st.site[k];
+      d.maxX = std::max<long long>(d.maxX, (long long)o.a * o.dhl * o.de * o.b * o.dhr);
+    }
+    if (st.kind != 1) continue;
+    for (int k = 1; k <= st.n - 2; ++k) {
+      const long long A = (long long)st.r[k - 1] * st.d[k];
+      d.maxM = std::max<long long>(d.maxM, A * st.D[k]);
+      d.maxL = std::max<long long>(d.maxL, A * A);
+      d.maxP = std::max<long long>(d.maxP, (long long)st.r[k] * st.D[k]);
+      d.maxLam = std::max<long long>(d.maxLam, A);
+    }
+  }
+  return d;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+Ws carve(tn_ctx* c, const Dims& d, int B, int nv) {
+  Ws w{};
+  w.sS = d.maxS; w.sY = d.maxY; w.sR = d.maxR; w.sX = d.maxX; w.sM = d.maxM;
+  w.sL = d.maxL; w.sP = d.maxP; w.sLam = d.maxLam; w.sAmax = d.maxN; w.sInv = nv;
+  const size_t dbl = sizeof(double);
+  size_t off[16];
+  size_t tot = 0;
+  const long long sizes[] = {w.sS, w.sS, w.sY, w.sR, w.sX, w.sM, w.sM, w.sL, w.sP, w.sLam, w.sInv};
+  for (int i = 0; i < 11; ++i) {
+    off[i] = tot;
+    tot += align256(dbl * size_t(sizes[i]) * B);
+  }
+  off[11] = tot;
+  tot += align256(sizeof(unsigned long long) * size_t(w.sAmax) * B);
+  char* base = static_cast<char*>(c->arena.get(tot));
+  double** outs[] = {&w.S0, &w.S1, &w.Y, &w.R, &w.X, &w.M, &w.G, &w.L, &w.P, &w.lam, &w.inv};
+  for (int i = 0; i < 11; ++i) *outs[i] = reinterpret_cast<double*>(base + off[i]);
+  w.amax = reinterpret_cast<unsigned long long*>(base + off[11]);
+  return w;
+}
+
+void ensure_results(tn_ctx* c, int B) {
+  char* base = static_cast<char*>(c->results.get(align256(sizeof(double) * B) * 2 +
+                                                 align256(sizeof(int) * B)));
+  c->logz = reinterpret_cast<double*>(base);
+  c->logscale = reinterpret_cast<double*>(base + align256(sizeof(double) * B));
+  c->status = reinterpret_cast<int*>(base + 2 * align256(sizeof(double) * B));
+}
+
+void* pinned_get(tn_ctx* c, size_t bytes) {
+  ck(cudaEventSynchronize(c->pinned_free), "cudaEventSynchronize");
+  if (bytes > c->pinned_cap) {
+    if (c->pinned) cudaFreeHost(c->pinned);
+    c->pinned = nullptr;
+    c->pinned_cap = 0;
+    if (cudaMallocHost(&c->pinned, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      fail(TN_ERR_OOM, "pinned host allocation failed");
+    }
+    c->pinned_cap = bytes;
+  }
+  return c->pinned;
+}
+
+// Device copies of the plan's per-step tables.
+struct StepTables {
+  tn::FuseSite* fuse;
+  int64_t* y_off;
+  int32_t* D;  // n + 1 entries (last = max D)
+};
+
+std::vector<StepTables> upload_tables(tn_ctx* c, const tn_plan_t* P, const double* const* tens_dev,
+                                      int B, const double*** tens_table, int64_t** off_dev,
+                                      int64_t** len_dev, cudaStream_t st) {
+  // layout: [tens ptrs B][site_off nv][site_len nv] then per step fuse/y_off/D
+  const int nv = P->n_vertices;
+  size_t tot = align256(sizeof(void*) * B) + 2 * align256(sizeof(int64_t) * nv);
+  std::vector<size_t> so(P->steps.size());
+  for (size_t s = 0; s < P->steps.size(); ++s) {
+    so[s] = tot;
+    const int n = P->steps[s].n;
+    tot += align256(sizeof(tn::FuseSite) * n) + align256(sizeof(int64_t) * n) +
+           align256(sizeof(int32_t) * (n + 1));
+  }
+  char* h = static_cast<char*>(pinned_get(c, tot));
+  char* dbase = static_cast<char*>(c->tables.get(tot));
+  std::memcpy(h, tens_dev, sizeof(void*) * B);
+  size_t o = align256(sizeof(void*) * B);
+  std::memcpy(h + o, P->site_off.data(), sizeof(int64_t) * nv);
+  *off_dev = reinterpret_cast<int64_t*>(dbase + o);
+  o += align256(sizeof(int64_t) * nv);
+  std::memcpy(h + o, P->site_len.data(), sizeof(int64_t) * nv);
+  *len_dev = reinterpret_cast<int64_t*>(dbase + o);
+  *tens_table = reinterpret_cast<const double**>(dbase);
+  std::vector<StepTables> out(P->steps.size());
+  for (size_t s = 0; s < P->steps.size(); ++s) {
+    const tn::Step& stp = P->steps[s];
+    const int n = stp.n;
+    size_t q = so[s];
+    tn::FuseSite* fh = reinterpret_cast<tn::FuseSite*>(h + q);
+    out[s].fuse = reinterpret_cast<tn::FuseSite*>(dbase + q);
+    for (int k = 0; k < n; ++k) {
+      const tn::SiteOp& op = stp.site[k];
+      tn::FuseSite f{};
+      f.vertex = op.vertex; f.a = op.a; f.dp = op.dp; f.b = op.b;
+      f.dhl = op.dhl; f.dhr = op.dhr; f.de = op.de;
+      f.t_off = op.t_off; f.sp = op.sp; f.shl = op.shl; f.shr = op.shr; f.se = op.se;
+      f.y_off = (stp.kind == 0) ? stp.s_off[k] : stp.y_off[k];
+      f.s_off = (s > 0) ? P->steps[s - 1].s_off[k] : 0;
+      fh[k] = f;
+    }
+    q += align256(sizeof(tn::FuseSite) * n);
+    std::memcpy(h + q, stp.y_off.data(), sizeof(int64_t) * n);
+    out[s].y_off = reinterpret_cast<int64_t*>(dbase + q);
+    q += align256(sizeof(int64_t) * n);
+    std::vector<int32_t> D(stp.D);
+    int mx = 1;
+    for (int x : D) mx = std::max(mx, x);
+    D.push_back(mx);
+    std::memcpy(h + q, D.data(), sizeof(int32_t) * (n + 1));
+    out[s].D = reinterpret_cast<int32_t*>(dbase + q);
+  }
+  ck(cudaMemcpyAsync(dbase, h, tot, cudaMemcpyHostToDevice, st), "upload tables");
+  ck(cudaEventRecord(c->pinned_free, st), "cudaEventRecord");
+  return out;
+}
+
+void gemm(bool ta, bool tb, const double* A, long long sA, int lda, const double* Bm, long long sB,
+          int ldb, double* C, long long sC, int ldc, int M, int N, int K, int batch,
+          const unsigned long long* amax_in, long long s_in, unsigned long long* amax_out,
+          long long s_out, cudaStream_t st) {
+  tn::GemmArgs g{};
+  g.A = A; g.sA = sA; g.lda = lda;
+  g.B = Bm; g.sB = sB; g.ldb = ldb;
+  g.C = C; g.sC = sC; g.ldc = ldc;
+  g.M = M; g.N = N; g.K = K; g.batch = batch;
+  g.amax_in = amax_in; g.s_amax_in = s_in;
+  g.amax_out = amax_out; g.s_amax_out = s_out;
+  ck(tn::launch_dgemm(ta, tb, g, st), "dgemm launch");
+}
+
+// One density_matrix_alg pass (Sec. 5) over the blocks in w.Y (layout of st),
+// writing the tree TN as boundary sites into Snext (layout st.s_off).
+void dm_pass(tn_ctx* c, const tn::Step& st, const Ws& w, double* Snext, int B, int precision,
+             cudaStream_t strm) {
+  (void)precision;
+  const int n = st.n;
+  const auto& D = st.D;
+  const auto& d = st.d;
+  // Memoised root-side density matrices, Eq. (dm_cache):
+  //   R_{n-1} = [1];  R_{k-1} = sum_e Y_k(:, e, :) R_k Y_k(:, e, :)^T  (k = n-1 .. 2)
+  // Each R_k is kept unnormalised; its running max-abs (amax[k]) scales the
+  // GEMM that consumes it, which keeps every R within range.
+  ck(cudaMemsetAsync(w.amax, 0, sizeof(unsigned long long) * w.sAmax * B, strm), "memset amax");
+  ck(tn::launch_fill_env_root(w.R + st.r_off[n - 1], w.sR, w.amax + (n - 1), w.sAmax, B, strm),
+     "env root");
+  for (int k = n - 1; k >= 2; --k) {
+    const double* Yk = w.Y + st.y_off[k];
+    const int Dl = D[k - 1], Dr = D[k], dk = d[k];
+    // X = Y_k (Dl*dk x Dr) . R_k / max|R_k|
+    gemm(false, false, Yk, w.sY, Dr, w.R + st.r_off[k], w.sR, Dr, w.X, w.sX, Dr, Dl * dk, Dr, Dr,
+         B, w.amax + k, w.sAmax, nullptr, 0, strm);
+    // R_{k-1} = X (Dl x dk*Dr) . Y_k(Dl x dk*Dr)^T
+    gemm(false, true, w.X, w.sX, dk * Dr, Yk, w.sY, dk * Dr, w.R + st.r_off[k - 1], w.sR, Dl, Dl,
+         Dl, dk * Dr, B, nullptr, 0, w.amax + (k - 1), w.sAmax, strm);
+  }
+  // Post-order over the MPS tree: vertices 1 .. n-2.
+  for (int k = 1; k <= n - 2; ++k) {
+    const int rp = st.r[k - 1], rk = st.r[k], dk = d[k], Dl = D[k - 1], Dr = D[k];
+    const int A = rp * dk;
+    const double* Pp = (k == 1) ? w.Y + st.y_off[0] : w.P;
+    const long long sPp = (k == 1) ? w.sY : w.sP;
+    // M_v = P_{v-1} . Y_v  -> (rp x dk*Dr) = (A x Dr)
+    gemm(false, false, Pp, sPp, Dl, w.Y + st.y_off[k], w.sY, dk * Dr, w.M, w.sM, dk * Dr, rp,
+         dk * Dr, Dl, B, nullptr, 0, nullptr, 0, strm);
+    // L_v = M_v R_k M_v^T  (R_k scaled by 1/max|R_k|)
+    gemm(false, false, w.M, w.sM, Dr, w.R + st.r_off[k], w.sR, Dr, w.G, w.sM, Dr, A, Dr, Dr, B,
+         w.amax + k, w.sAmax, nullptr, 0, strm);
+    gemm(false, true, w.G, w.sM, Dr, w.M, w.sM, Dr, w.L, w.sL, A, A, A, Dr, B, nullptr, 0, nullptr,
+         0, strm);
+    // U_v = leading_eigenvectors(L_v, r_k), written as boundary site k
+    double* Uk = Snext + st.s_off[k];
+    ck(tn::launch_eigh_top<double>(w.L, w.sL, Uk, w.sS, w.lam, w.sLam, A, rk, 0, c->status, B,
+                                   strm),
+       "eigh launch");
+    // P_v = U_v^T M_v  (rk x Dr)
+    gemm(true, false, Uk, w.sS, rk, w.M, w.sM, Dr, w.P, w.sP, Dr, rk, Dr, A, B, nullptr, 0,
+         nullptr, 0, strm);
+  }
+  // Root: M_r = P_{n-2} . Y_{n-1}, scaled to unit norm into the log-scale.
+  ck(tn::launch_root(w.P, w.sP, w.Y + st.y_off[n - 1], w.sY, st.r[n - 2], D[n - 2], d[n - 1],
+                     Snext + st.s_off[n - 1], Snext + st.s_off[0], d[0], w.sS, c->logscale,
+                     c->status, B, strm),
+     "root launch");
+}
+
+void run_plan(tn_ctx* c, const tn_plan_t* P, int B, const double* const* tens_dev, int precision,
+              cudaStream_t strm) {
+  if (precision != TN_PREC_FP64)
+    fail(TN_ERR_UNSUPPORTED, "this build runs the FP64 path only (precision 0)");
+  const Dims dm = plan_dims(P);
+  ensure_results(c, B);
+  const Ws w = carve(c, dm, B, P->n_vertices);
+  const double** tens_table = nullptr;
+  int64_t *off_dev = nullptr, *len_dev = nullptr;
+  std::vector<StepTables> tabs =
+      upload_tables(c, P, tens_dev, B, &tens_table, &off_dev, &len_dev, strm);
+  ck(tn::launch_site_norm(tens_table, off_dev, len_dev, P->n_vertices, B, w.inv, c->logscale,
+                          c->status, strm),
+     "site norm");
+  double* Scur = w.S0;
+  double* Snext = w.S1;
+  for (size_t s = 0; s < P->steps.size(); ++s) {
+    const tn::Step& st = P->steps[s];
+    int maxe = 1;
+    for (int k = 0; k < st.n; ++k) {
+      const tn::SiteOp& o = st.site[k];
+      maxe = std::max<int>(maxe, o.a * o.dhl * o.de * o.b * o.dhr);
+    }
+    if (st.kind == 0) {
+      ck(tn::launch_fuse(tabs[s].fuse, st.n, maxe, tens_table, w.inv, P->n_vertices, nullptr, 0, 1,
+                         Snext, w.sS, B, strm),
+         "fuse");
+      std::swap(Scur, Snext);
+    } else if (st.kind == 1) {
+      ck(tn::launch_fuse(tabs[s].fuse, st.n, maxe, tens_table, w.inv, P->n_vertices, Scur, w.sS, 0,
+                         w.Y, w.sY, B, strm),
+         "fuse");
+      dm_pass(c, st, w, Snext, B, precision, strm);
+      std::swap(Scur, Snext);
+    } else {
+      ck(tn::launch_fuse(tabs[s].fuse, st.n, maxe, tens_table, w.inv, P->n_vertices, Scur, w.sS, 0,
+                         w.Y, w.sY, B, strm),
+         "fuse");
+      int maxD = 1;
+      for (int k = 0; k < st.n; ++k) maxD = std::max(maxD, st.D[k]);
+      ck(tn::launch_close(w.Y, w.sY, tabs[s].y_off, tabs[s].D, st.n, maxD, c->logscale, c->logz,
+                          c->status, B, strm),
+         "close");
+    }
+  }
+  c->stream = strm;
+  c->last_batch = B;
+  c->pending = true;
+}
+
+template <class F>
+tn_status guarded(tn_ctx* c, const char* fn, F&& f) {
+  try {
+    f();
+  } catch (const Fail& e) {
+    const std::string m = std::string(fn) + ": " + e.msg;
+    if (c) c->err = m;
+    tn::set_error(m);
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    const std::string m = std::string(fn) + ": host allocation failed";
+    if (c) c->err = m;
+    tn::set_error(m);
+    return TN_ERR_OOM;
+  } catch (...) {
+    const std::string m = std::string(fn) + ": unexpected error";
+    if (c) c->err = m;
+    tn::set_error(m);
+    return TN_ERR_INVALID;
+  }
+  return TN_OK;
+}
+
+}  // namespace
+
+extern "C" tn_status tn_ctx_create(int32_t device, tn_ctx_t** out) {
+  if (!out) {
+    tn::set_error("tn_ctx_create: out is NULL");
+    return TN_ERR_INVALID;
+  }
+  *out = nullptr;
+  tn_ctx* c = new (std::nothrow) tn_ctx();
+  if (!c) {
+    tn::set_error("tn_ctx_create: host allocation failed");
+    return TN_ERR_OOM;
+  }
+  tn_status s = guarded(nullptr, "tn_ctx_create", [&] {
+    int n = 0;
+    ck(cudaGetDeviceCount(&n), "cudaGetDeviceCount");
+    if (device < 0 || device >= n) fail(TN_ERR_INVALID, "device ordinal out of range");
+    ck(cudaSetDevice(device), "cudaSetDevice");
+    c->device = device;
+    ck(cudaEventCreateWithFlags(&c->pinned_free, cudaEventDisableTiming), "cudaEventCreate");
+    ck(tn::eigh_configure(), "eigh configure");
+  });
+  if (s != TN_OK) {
+    delete c;
+    return s;
+  }
+  *out = c;
+  return TN_OK;
+}
+
+extern "C" tn_status tn_ctx_destroy(tn_ctx_t* c) {
+  if (!c) return TN_OK;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  c->arena.release();
+  c->stage.release();
+  c->tables.release();
+  c->results.release();
+  if (c->pinned) cudaFreeHost(c->pinned);
+  if (c->pinned_free) cudaEventDestroy(c->pinned_free);
+  delete c;
+  return TN_OK;
+}
+
+extern "C" tn_status tn_contract_approx(tn_ctx_t* c, const tn_plan_t* const* plans, int32_t n_inst,
+                                        const double* const* sites_dev, int32_t precision,
+                                        int32_t learned_chi, void* stream) {
+  if (!c) {
+    tn::set_error("tn_contract_approx: ctx is NULL");
+    return TN_ERR_INVALID;
+  }
+  return guarded(c, "tn_contract_approx", [&] {
+    if (!plans || !sites_dev || n_inst < 1) fail(TN_ERR_INVALID, "plans/sites NULL or n_inst < 1");
+    if (learned_chi) fail(TN_ERR_UNSUPPORTED, "learned chi is not available in this build");
+    for (int i = 0; i < n_inst; ++i) {
+      if (!plans[i] || !sites_dev[i]) fail(TN_ERR_INVALID, "NULL plan or site buffer");
+      if (!tn::plans_equivalent(plans[0], plans[i]))
+        fail(TN_ERR_UNSUPPORTED, "instances of one batch must share the plan structure");
+    }
+    ck(cudaSetDevice(c->device), "cudaSetDevice");
+    run_plan(c, plans[0], n_inst, sites_dev, precision, static_cast<cudaStream_t>(stream));
+  });
+}
+
+extern "C" tn_status tn_logz(tn_ctx_t* c, double* logz_host, int32_t* status_host, int32_t n_inst) {
+  if (!c) {
+    tn::set_error("tn_logz: ctx is NULL");
+    return TN_ERR_INVALID;
+  }
+  tn_status first = TN_OK;
+  tn_status s = guarded(c, "tn_logz", [&] {
+    if (!c->pending) fail(TN_ERR_INVALID, "no batch has been launched");
+    if (n_inst != c->last_batch) fail(TN_ERR_INVALID, "n_inst differs from the launched batch");
+    if (!logz_host || !status_host) fail(TN_ERR_INVALID, "NULL output");
+    ck(cudaSetDevice(c->device), "cudaSetDevice");
+    ck(cudaMemcpyAsync(logz_host, c->logz, sizeof(double) * n_inst, cudaMemcpyDeviceToHost,
+                       c->stream),
+       "copy logz");
+    ck(cudaMemcpyAsync(status_host, c->status, sizeof(int) * n_inst, cudaMemcpyDeviceToHost,
+                       c->stream),
+       "copy status");
+    ck(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    for (int i = 0; i < n_inst; ++i)
+      if (status_host[i] != TN_OK && first == TN_OK) first = tn_status(status_host[i]);
+    if (first != TN_OK) {
+      c->err = "tn_logz: instance failed with status " + std::to_string(int(first));
+      tn::set_error(c->err);
+    }
+  });
+  return s != TN_OK ? s : first;
+}
+
+extern "C" tn_status tn_contract_approx_host(tn_ctx_t* c, const tn_plan_t* const* plans,
+                                             int32_t n_inst, const double* const* sites_host,
+                                             int32_t precision, int32_t learned_chi,
+                                             double* logz_host, int32_t* status_host,
+                                             void* stream) {
+  if (!c) {
+    tn::set_error("tn_contract_approx_host: ctx is NULL");
+    return TN_ERR_INVALID;
+  }
+  tn_status s = guarded(c, "tn_contract_approx_host", [&] {
+    if (!plans || !sites_host || n_inst < 1 || !plans[0])
+      fail(TN_ERR_INVALID, "plans/sites NULL or n_inst < 1");
+    ck(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t per = plans[0]->site_elems;
+    double* dev = static_cast<double*>(c->stage.get(sizeof(double) * size_t(per) * n_inst));
+    std::vector<const double*> ptrs(n_inst);
+    for (int i = 0; i < n_inst; ++i) {
+      if (!sites_host[i]) fail(TN_ERR_INVALID, "NULL site buffer");
+      ck(cudaMemcpyAsync(dev + per * i, sites_host[i], sizeof(double) * per,
+                         cudaMemcpyHostToDevice, st),
+         "copy sites");
+      ptrs[i] = dev + per * i;
+    }
+    tn_status r = tn_contract_approx(c, plans, n_inst, ptrs.data(), precision, learned_chi, stream);
+    if (r != TN_OK) fail(r, c->err);
+  });
+  if (s != TN_OK) return s;
+  return tn_logz(c, logz_host, status_host, n_inst);
+}
+
+extern "C" tn_status tn_embed_tree(tn_ctx_t* c, int32_t n_inst, int32_t n_legs,
+                                   const int32_t* leg_dim, const int32_t* bond_dim,
+                                   const double* const* blocks_dev, int32_t chi,
+                                   const int32_t* chi_per_edge, int32_t precision,
+                                   double* const* tree_dev, double* lognorm_dev,
+                                   int32_t* status_dev, int32_t* ranks_host, void* stream) {
+  if (!c) {
+    tn::set_error("tn_embed_tree: ctx is NULL");
+    return TN_ERR_INVALID;
+  }
+  return guarded(c, "tn_embed_tree", [&] {
+    if (n_inst < 1 || n_legs < 3 || !leg_dim || !bond_dim || !blocks_dev || !tree_dev ||
+        !lognorm_dev || !status_dev || !ranks_host)
+      fail(TN_ERR_INVALID, "invalid argument");
+    if (chi < 1 && !chi_per_edge) fail(TN_ERR_INVALID, "chi must be >= 1");
+    if (precision != TN_PREC_FP64)
+      fail(TN_ERR_UNSUPPORTED, "this build runs the FP64 path only (precision 0)");
+    const int n = n_legs;
+    tn::Step st;
+    st.kind = 1;
+    st.n = n;
+    st.d.assign(leg_dim, leg_dim + n);
+    st.D.assign(n, 1);
+    for (int k = 0; k < n; ++k) {
+      if (st.d[k] < 1) fail(TN_ERR_INVALID, "leg dim < 1");
+      if (k < n - 1) {
+        st.D[k] = bond_dim[k];
+        if (st.D[k] < 1 || st.D[k] > (1 << 16)) fail(TN_ERR_INVALID, "bond dim out of range");
+      }
+    }
+    st.site.resize(n);
+    for (int k = 0; k < n; ++k) {
+      tn::SiteOp o{};
+      o.a = (k == 0) ? 1 : st.D[k - 1];
+      o.b = st.D[k];
+      o.dp = o.dhl = o.dhr = 1;
+      o.de = st.d[k];
+      st.site[k] = o;
+    }
+    st.r.assign(n - 1, 0);
+    st.r[0] = st.d[0];
+    for (int k = 1; k <= n - 2; ++k) {
+      double beyond = 1;
+      for (int j = k + 1; j < n; ++j) beyond *= st.d[j];
+      const int ck_ = chi_per_edge ? chi_per_edge[k] : chi;
+      if (ck_ < 1) fail(TN_ERR_INVALID, "chi_per_edge entries must be >= 1");
+      double r = std::min<double>(ck_, double(st.r[k - 1]) * st.d[k]);
+      r = std::min<double>(r, st.D[k]);
+      r = std::min<double>(r, beyond);
+      st.r[k] = int(r);
+    }
+    // layouts identical to the planner's
+    st.y_off.assign(n, 0);
+    long long off = 0;
+    for (int k = 0; k < n; ++k) {
+      st.y_off[k] = off;
+      off += (long long)st.site[k].a * st.d[k] * st.D[k];
+    }
+    st.y_total = off;
+    st.s_off.assign(n, 0);
+    st.s_size.assign(n, 0);
+    off = 0;
+    for (int k = 0; k < n; ++k) {
+      const long long left = (k == 0) ? 1 : st.r[k - 1];
+      const long long right = (k == n - 1) ? 1 : st.r[k];
+      st.s_off[k] = off;
+      st.s_size[k] = left * st.d[k] * right;
+      off += st.s_size[k];
+    }
+    st.s_total = off;
+    st.r_off.assign(n, 0);
+    off = 0;
+    for (int k = 1; k <= n - 1; ++k) {
+      st.r_off[k] = off;
+      off += (long long)st.D[k] * st.D[k];
+    }
+    st.r_total = off;
+    tn_plan_t tmp;
+    tmp.steps.push_back(st);
+    const Dims dm = plan_dims(&tmp);
+    ck(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t strm = static_cast<cudaStream_t>(stream);
+    ensure_results(c, n_inst);
+    const Ws w = carve(c, dm, n_inst, 1);
+    ck(cudaMemsetAsync(c->logscale, 0, sizeof(double) * n_inst, strm), "memset");
+    ck(cudaMemsetAsync(c->status, 0, sizeof(int) * n_inst, strm), "memset");
+    for (int i = 0; i < n_inst; ++i)
+      ck(cudaMemcpyAsync(w.Y + w.sY * i, blocks_dev[i], sizeof(double) * st.y_total,
+                         cudaMemcpyDeviceToDevice, strm),
+         "copy blocks");
+    dm_pass(c, st, w, w.S1, n_inst, precision, strm);
+    for (int i = 0; i < n_inst; ++i)
+      ck(cudaMemcpyAsync(tree_dev[i], w.S1 + w.sS * i + st.s_off[1],
+                         sizeof(double) * (st.s_total - st.s_size[0]), cudaMemcpyDeviceToDevice,
+                         strm),
+         "copy tree");
+    ck(cudaMemcpyAsync(lognorm_dev, c->logscale, sizeof(double) * n_inst,
+                       cudaMemcpyDeviceToDevice, strm),
+       "copy lognorm");
+    ck(cudaMemcpyAsync(status_dev, c->status, sizeof(int) * n_inst, cudaMemcpyDeviceToDevice,
+                       strm),
+       "copy status");
+    for (int k = 0; k < n - 1; ++k) ranks_host[k] = st.r[k];
+  });
+}
+
+extern "C" const char* tn_last_error(const tn_ctx_t* c) {
+  if (c && !c->err.empty()) return c->err.c_str();
+  return tn::get_error();
+}

@@ -1,0 +1,382 @@
+// Batched top-r symmetric eigensolver for the density matrices L_v
+// (leading_eigenvectors of Algorithm density_matrix_alg, Sec. 5).
+//
+// One CTA per matrix, everything in shared memory:
+//   1. Householder reduction to tridiagonal form, A = Q T Q^T
+//      (Golub & Van Loan, Matrix Computations, Sec. 8.3.1);
+//   2. the wanted eigenvalues of T by Sturm-sequence bisection, one thread per
+//      eigenvalue (Barth, Martin & Wilkinson 1967);
+//   3. eigenvectors of T by inverse iteration with partial-pivoting LU of
+//      T - lambda I (Wilkinson), one thread per eigenvector, shifts of
+//      near-equal eigenvalues separated as in LAPACK's stein;
+//   4. modified Gram-Schmidt over the r vectors (descending eigenvalue order);
+//   5. back-transformation by the stored reflectors, U = Q Z;
+//   6. each column signed so that its largest-|.| entry (first on ties) is
+//      positive.
+// Every loop has a fixed iteration bound; nothing waits on other blocks.
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cmath>
+#include <cstdint>
+
+#include "kernels.cuh"
+#include "tn_dmtree.h"
+
+namespace tn {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kNmax = 128;
+
+template <typename T> struct Lim;
+template <> struct Lim<double> {
+  __device__ static double eps() { return DBL_EPSILON * 0.5; }
+  __device__ static double safmin() { return DBL_MIN; }
+  static constexpr int maxit = 80;
+};
+template <> struct Lim<float> {
+  __device__ static float eps() { return FLT_EPSILON * 0.5f; }
+  __device__ static float safmin() { return FLT_MIN; }
+  static constexpr int maxit = 40;
+};
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  T t = (lane < (kThreads >> 5)) ? red[lane] : T(0);
+  t = warp_sum(t);
+  return t;
+}
+
+template <typename T>
+__device__ int sturm_count(const T* dd, const T* e2, int n, T x, T pivmin) {
+  T q = dd[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  int c = (q < T(0));
+  for (int j = 1; j < n; ++j) {
+    q = dd[j] - x - e2[j - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    c += (q < T(0));
+  }
+  return c;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_eigh_top(const T* __restrict__ Lg, long long sL,
+                                                       double* __restrict__ Ug, long long sU,
+                                                       double* __restrict__ lamg, long long slam,
+                                                       int n, int r, int nlam, int* status) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  __shared__ T red[32];
+  __shared__ T scal[8];
+  const int ld = n + 1;
+  const int nl = (nlam > r) ? nlam : r;
+  T* A = reinterpret_cast<T*>(raw);   // n x ld
+  T* Z = A + n * ld;                   // r vectors of length n (column-major)
+  T* dd = Z + n * r;
+  T* ee = dd + n;
+  T* e2 = ee + n;
+  T* tau = e2 + n;
+  T* v = tau + n;
+  T* w = v + n;
+  T* lam = w + n;                      // nl
+  T* shift = lam + nl;                 // r
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = kThreads >> 5;
+  const int b = blockIdx.x;
+  const T* L = Lg + (long long)b * sL;
+
+  // ---- load, symmetrise, screen for NaN/Inf
+  bool bad = false;
+  for (int idx = tid; idx < n * n; idx += kThreads) {
+    const int a = idx / n, c = idx % n;
+    const T x = T(0.5) * (L[(long long)a * n + c] + L[(long long)c * n + a]);
+    if (!isfinite(x)) bad = true;
+    A[a * ld + c] = x;
+  }
+  if (__syncthreads_or(bad)) {
+    double* U = Ug + (long long)b * sU;
+    for (int idx = tid; idx < n * r; idx += kThreads) U[idx] = 0.0;
+    if (tid == 0) status[b] = TN_ERR_NONFINITE;
+    return;
+  }
+
+  // ---- 1. Householder tridiagonalisation (lower), v stored below the diagonal
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;
+    T part = T(0);
+    for (int j = 1 + tid; j < m; j += kThreads) {
+      const T x = A[(k + 1 + j) * ld + k];
+      part += x * x;
+    }
+    const T sig = block_sum(part, red);
+    if (tid == 0) {
+      dd[k] = A[k * ld + k];
+      const T alpha = A[(k + 1) * ld + k];
+      if (sig == T(0)) {
+        tau[k] = T(0);
+        ee[k] = alpha;
+        scal[0] = T(0);
+      } else {
+        const T beta = -copysign(sqrt(alpha * alpha + sig), alpha);
+        tau[k] = (beta - alpha) / beta;
+        ee[k] = beta;
+        scal[0] = T(1) / (alpha - beta);
+      }
+    }
+    __syncthreads();
+    const T tk = tau[k];
+    if (tk == T(0)) {
+      for (int j = tid; j < m; j += kThreads) A[(k + 1 + j) * ld + k] = (j == 0) ? T(1) : T(0);
+      __syncthreads();
+      continue;
+    }
+    const T sc = scal[0];
+    for (int j = tid; j < m; j += kThreads) {
+      const T x = (j == 0) ? T(1) : A[(k + 1 + j) * ld + k] * sc;
+      v[j] = x;
+      A[(k + 1 + j) * ld + k] = x;
+    }
+    __syncthreads();
+    // w = tau * A22 v (warp per row)
+    for (int a = warp; a < m; a += nwarp) {
+      const T* row = A + (k + 1 + a) * ld + (k + 1);
+      T s = T(0);
+      for (int c = lane; c < m; c += 32) s += row[c] * v[c];
+      s = warp_sum(s);
+      if (lane == 0) w[a] = tk * s;
+    }
+    __syncthreads();
+    T pd = T(0);
+    for (int a = tid; a < m; a += kThreads) pd += w[a] * v[a];
+    const T dot = block_sum(pd, red);
+    const T K = T(-0.5) * tk * dot;
+    for (int a = tid; a < m; a += kThreads) w[a] += K * v[a];
+    __syncthreads();
+    for (int idx = tid; idx < m * m; idx += kThreads) {
+      const int a = idx / m, c = idx % m;
+      A[(k + 1 + a) * ld + (k + 1 + c)] -= v[a] * w[c] + w[a] * v[c];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (n >= 2) {
+      dd[n - 2] = A[(n - 2) * ld + (n - 2)];
+      ee[n - 2] = A[(n - 1) * ld + (n - 2)];
+      tau[n - 2] = T(0);
+    }
+    dd[n - 1] = A[(n - 1) * ld + (n - 1)];
+    ee[n - 1] = T(0);
+    // Gershgorin interval, pivmin (LAPACK stebz conventions)
+    T gl = dd[0], gu = dd[0], emax = T(0);
+    for (int j = 0; j < n; ++j) {
+      const T el = (j > 0) ? fabs(ee[j - 1]) : T(0);
+      const T er = (j + 1 < n) ? fabs(ee[j]) : T(0);
+      gl = fmin(gl, dd[j] - el - er);
+      gu = fmax(gu, dd[j] + el + er);
+      if (j + 1 < n) {
+        e2[j] = ee[j] * ee[j];
+        emax = fmax(emax, e2[j]);
+      }
+    }
+    const T tnorm = fmax(fabs(gl), fabs(gu));
+    const T eps = Lim<T>::eps();
+    const T pivmin = Lim<T>::safmin() * fmax(T(1), emax);
+    gl -= T(2.1) * tnorm * eps * n + T(4.2) * pivmin;
+    gu += T(2.1) * tnorm * eps * n + T(4.2) * pivmin;
+    scal[1] = gl;
+    scal[2] = gu;
+    scal[3] = tnorm;
+    scal[4] = pivmin;
+  }
+  __syncthreads();
+  const T gl = scal[1], gu = scal[2], tnorm = scal[3], pivmin = scal[4];
+  const T eps = Lim<T>::eps();
+
+  // ---- 2. bisection for the nl largest eigenvalues (descending)
+  if (tid < nl && tid < n) {
+    const int j = n - 1 - tid;  // ascending index
+    T lo = gl, hi = gu;
+    for (int it = 0; it < Lim<T>::maxit; ++it) {
+      const T mid = T(0.5) * (lo + hi);
+      if (hi - lo <= T(2) * eps * fmax(fabs(lo), fabs(hi)) + T(2) * pivmin) break;
+      if (sturm_count(dd, e2, n, mid, pivmin) <= j) lo = mid;
+      else hi = mid;
+    }
+    lam[tid] = T(0.5) * (lo + hi);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    // separate near-equal shifts (descending order)
+    const T pertol = T(10) * eps * fmax(tnorm, Lim<T>::safmin());
+    for (int t = 0; t < r; ++t) {
+      T s = lam[t];
+      if (t > 0 && shift[t - 1] - s < pertol) s = shift[t - 1] - pertol;
+      shift[t] = s;
+    }
+  }
+  __syncthreads();
+
+  // ---- 3. inverse iteration, one thread per eigenvector
+  if (tid < r) {
+    T u1[kNmax], u2[kNmax], u3[kNmax], ml[kNmax], x[kNmax];
+    unsigned char pv[kNmax];
+    const T lmb = shift[tid];
+    const T tp = fmax(eps * tnorm, Lim<T>::safmin());
+    T a = dd[0] - lmb;
+    T bb = (n > 1) ? ee[0] : T(0);
+    for (int k = 0; k + 1 < n; ++k) {
+      const T c = ee[k];
+      const T nd = dd[k + 1] - lmb;
+      const T ns = (k + 2 < n) ? ee[k + 1] : T(0);
+      if (fabs(a) >= fabs(c)) {
+        if (a == T(0)) a = tp;
+        const T mlt = c / a;
+        pv[k] = 0; ml[k] = mlt; u1[k] = a; u2[k] = bb; u3[k] = T(0);
+        a = nd - mlt * bb;
+        bb = ns;
+      } else {
+        const T mlt = a / c;
+        pv[k] = 1; ml[k] = mlt; u1[k] = c; u2[k] = nd; u3[k] = ns;
+        a = bb - mlt * nd;
+        bb = -mlt * ns;
+      }
+    }
+    if (a == T(0)) a = tp;
+    u1[n - 1] = a;
+    // deterministic start vector
+    for (int k = 0; k < n; ++k) {
+      unsigned int h = 2654435761u * (unsigned)(k + 1) ^ (40503u * (unsigned)(tid + 7));
+      h ^= h >> 13; h *= 0x5bd1e995u; h ^= h >> 15;
+      x[k] = T(1) + T(0.5) * (T(h & 0xffff) / T(65536) - T(0.5));
+    }
+    for (int it = 0; it < 3; ++it) {
+      for (int k = 0; k + 1 < n; ++k) {
+        if (pv[k]) { const T t = x[k]; x[k] = x[k + 1]; x[k + 1] = t; }
+        x[k + 1] -= ml[k] * x[k];
+      }
+      x[n - 1] = x[n - 1] / u1[n - 1];
+      if (n >= 2) x[n - 2] = (x[n - 2] - u2[n - 2] * x[n - 1]) / u1[n - 2];
+      for (int k = n - 3; k >= 0; --k) x[k] = (x[k] - u2[k] * x[k + 1] - u3[k] * x[k + 2]) / u1[k];
+      T mx = T(0);
+      for (int k = 0; k < n; ++k) mx = fmax(mx, fabs(x[k]));
+      const T inv = (mx > T(0) && isfinite(mx)) ? T(1) / mx : T(1);
+      for (int k = 0; k < n; ++k) x[k] *= inv;
+    }
+    T* zc = Z + tid * n;
+    for (int k = 0; k < n; ++k) zc[k] = x[k];
+  }
+  __syncthreads();
+
+  // ---- 4. modified Gram-Schmidt (descending eigenvalue order)
+  for (int j = 0; j < r; ++j) {
+    T* zj = Z + j * n;
+    T part = T(0);
+    for (int a = tid; a < n; a += kThreads) part += zj[a] * zj[a];
+    const T nrm = sqrt(block_sum(part, red));
+    const T inv = (nrm > T(0)) ? T(1) / nrm : T(0);
+    for (int a = tid; a < n; a += kThreads) zj[a] *= inv;
+    __syncthreads();
+    for (int c = j + 1 + warp; c < r; c += nwarp) {
+      T* zc = Z + c * n;
+      T s = T(0);
+      for (int a = lane; a < n; a += 32) s += zj[a] * zc[a];
+      s = warp_sum(s);
+      for (int a = lane; a < n; a += 32) zc[a] -= s * zj[a];
+    }
+    __syncthreads();
+  }
+
+  // ---- 5. back-transformation U = H_0 H_1 ... H_{n-3} Z
+  for (int k = n - 3; k >= 0; --k) {
+    const T tk = tau[k];
+    if (tk == T(0)) continue;  // uniform across the block
+    const int m = n - k - 1;
+    const T* vk = A + (k + 1) * ld + k;  // vk[j * ld] = v_j
+    for (int c = warp; c < r; c += nwarp) {
+      T* zc = Z + c * n + (k + 1);
+      T s = T(0);
+      for (int a = lane; a < m; a += 32) s += vk[a * ld] * zc[a];
+      s = tk * warp_sum(s);
+      __syncwarp();
+      for (int a = lane; a < m; a += 32) zc[a] -= s * vk[a * ld];
+    }
+    __syncthreads();
+  }
+
+  // ---- 6. sign convention and output
+  for (int c = warp; c < r; c += nwarp) {
+    T* zc = Z + c * n;
+    T best = T(-1);
+    int bi = n;
+    for (int a = lane; a < n; a += 32) {
+      const T x = fabs(zc[a]);
+      if (x > best || (x == best && a < bi)) { best = x; bi = a; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    const T sgn = (bi < n && zc[bi] < T(0)) ? T(-1) : T(1);
+    __syncwarp();
+    for (int a = lane; a < n; a += 32) zc[a] *= sgn;
+  }
+  __syncthreads();
+  double* U = Ug + (long long)b * sU;
+  for (int idx = tid; idx < n * r; idx += kThreads) {
+    const int a = idx / r, c = idx % r;
+    U[idx] = double(Z[c * n + a]);
+  }
+  if (lamg) {
+    double* lo = lamg + (long long)b * slam;
+    for (int t = tid; t < nlam && t < n; t += kThreads) lo[t] = double(lam[t]);
+  }
+}
+
+}  // namespace
+
+template <typename T>
+size_t eigh_smem_bytes(int n, int r, int nlam) {
+  const int nl = nlam > r ? nlam : r;
+  return sizeof(T) * (size_t(n) * (n + 1) + size_t(n) * r + 7 * size_t(n) + nl + r);
+}
+
+template <typename T>
+cudaError_t launch_eigh_top(const T* L, long long sL, double* U, long long sU, double* lam,
+                            long long slam, int n, int r, int nlam, int* status, int batch,
+                            cudaStream_t st) {
+  if (n < 1 || n > kNmax || r < 1 || r > n || nlam > n) return cudaErrorInvalidValue;
+  const size_t smem = eigh_smem_bytes<T>(n, r, nlam);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  k_eigh_top<T><<<batch, kThreads, smem, st>>>(L, sL, U, sU, lam, slam, n, r, nlam, status);
+  return cudaGetLastError();
+}
+
+cudaError_t eigh_configure() {
+  cudaError_t e = cudaFuncSetAttribute(k_eigh_top<double>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_eigh_top<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              227 * 1024);
+}
+
+template size_t eigh_smem_bytes<double>(int, int, int);
+template size_t eigh_smem_bytes<float>(int, int, int);
+template cudaError_t launch_eigh_top<double>(const double*, long long, double*, long long, double*,
+                                             long long, int, int, int, int*, int, cudaStream_t);
+template cudaError_t launch_eigh_top<float>(const float*, long long, double*, long long, double*,
+                                            long long, int, int, int, int*, int, cudaStream_t);
+
+}  // namespace tn
