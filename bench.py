@@ -1,0 +1,382 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the density-matrix tree approximation on one node.
+
+Workload: the 2D Ising spin glass on a 32 x 32 open lattice, couplings
+J_ij ~ N(0, 1) from the seeded generator, beta = 0.5, bond dim 2, rows as
+partitions, MPS ansatz, chi = 64; one "step" contracts a batch of B instances
+(default B = 2 x 152) from site tensors to ln Z.  Metric: approximate
+contractions per second (whole job; weak scaling: every rank owns B
+instances).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|tf32|bf16]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
+
+Timing: each timed step is bracketed by CUDA events on the launching stream;
+a 256 MB buffer is rewritten between steps (L2 flush, outside the events);
+barrier + synchronize on both sides; the max over ranks is reported.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+# Peaks used for roofline fractions.  Tensor peaks come from the measured
+# copy / cuBLAS numbers when available; ALU peaks are derived from unit counts
+# and clocks: FP32 = 152 SMs x 128 lanes x 2 flop x 2.07 GHz; FP64 = the
+# part's nominal 1.25 TFLOP/s.
+FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_ALU_TFLOPS = 1.25
+TF32_PER_BF16 = 1.1 / 2.25
+
+WORKLOAD = "2D Ising spin glass 32x32 open, J~N(0,1), beta=0.5, rows as partitions, MPS ansatz"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "bf16"])
+    p.add_argument("--chi", type=int, default=64)
+    p.add_argument("--size", type=int, default=32)
+    p.add_argument("--batch", type=int, default=304)
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(FALLBACK), "fallback"
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu_id)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------- workload
+
+def make_instances(first, count, size):
+    from workloads import ising
+    return [ising.lattice2d(size, size, 0.5, "gauss", seed=2 * 10**6 + first + i)
+            for i in range(count)]
+
+
+def pack_all(B, plan, ws):
+    info = B.tn_plan_query(plan)
+    n = len(ws[0]["tensors"])
+    offs = [B.tn_plan_site_offset(plan, v) for v in range(n)]
+    buf = np.empty((len(ws), info["site_elems"]), dtype=np.float64)
+    for i, w in enumerate(ws):
+        for v, t in enumerate(w["tensors"]):
+            buf[i, offs[v]:offs[v] + t.size] = t.reshape(-1)
+    return buf
+
+
+# ------------------------------------------------------------ cpu oracle
+
+_ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+from oracle import dmtree
+from workloads import ising
+t0 = time.perf_counter(); out = []
+i = 0
+while True:
+    w = ising.lattice2d({size}, {size}, 0.5, "gauss", seed=2 * 10**6 + {first} + i)
+    r = dmtree.partitioned_contract_rows(w, {chi})
+    out.append(r["logz"]); i += 1
+    el = time.perf_counter() - t0
+    if i >= {max_inst} or (el >= {seconds} and i >= {min_inst}):
+        break
+print(json.dumps({{"instances": i, "seconds": time.perf_counter() - t0, "logz": out}}))
+"""
+
+
+def run_oracle(first, size, chi, seconds, min_inst=1, max_inst=10**6):
+    cores = os.cpu_count() or 1
+    env = dict(os.environ)
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(cores)
+    code = _ORACLE_SNIPPET.format(root=ROOT, size=size, first=first, chi=chi, seconds=seconds,
+                                  min_inst=min_inst, max_inst=max_inst)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    d["cores"] = cores
+    return d
+
+
+# ------------------------------------------------------------ reference arm
+
+def bench_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    K, W = args.steps, args.warmup
+    per_step = 2
+    for wi in range(W):
+        run_oracle(10**5 + wi, args.size, args.chi, 0.0, 1, 1)
+    total_s, total_inst, cores = 0.0, 0, 1
+    for k in range(K):
+        d = run_oracle(k * per_step, args.size, args.chi, 0.0, per_step, per_step)
+        total_s += d["seconds"]
+        total_inst += d["instances"]
+        cores = d["cores"]
+    value = total_inst / total_s
+    line = {
+        "impl": "reference", "metric": "approx contractions/s", "value": value,
+        "unit": "contractions/s", "n_gpus": args.gpus, "steps": K, "warmup": W,
+        "ms_per_step": 1e3 * total_s / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "chi": args.chi, "size": args.size,
+                   "batch": per_step, "l2": "n/a (CPU)"},
+        "e2e": {"value": value, "unit": "contractions/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "cpu_baseline": {"value": value, "unit": "contractions/s", "cores": cores,
+                         "kind": "oracle",
+                         "sample": f"{per_step} instances per step of the {args.size}x{args.size} "
+                                   f"chi={args.chi} workload, FP64 numpy oracle"},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ ours
+
+def bench_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2406_09769_gb300 import binding as B
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = {"fp64": B.TN_PREC_FP64, "tf32": B.TN_PREC_TF32, "bf16": B.TN_PREC_BF16}[args.precision]
+    Bn, K, W = args.batch, args.steps, args.warmup
+
+    # workload (rank r owns instances r*B .. r*B+B-1)
+    ws = make_instances(rank * Bn, Bn, args.size)
+    w0 = ws[0]
+    plan = B.tn_plan(w0["n"], w0["edges"], np.full(len(w0["edges"]), 2), args.chi,
+                     env_size=args.size)
+    info = B.tn_plan_query(plan)
+    host = pack_all(B, plan, ws)
+    sites = torch.from_numpy(host).to(dev)
+    elems = host.shape[1]
+    ptrs = [sites.data_ptr() + 8 * elems * i for i in range(Bn)]
+    plans = [plan] * Bn
+    ctx = B.tn_ctx_create(local)
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def step():
+        B.tn_contract_approx(ctx, plans, ptrs, prec, 0, sh)
+
+    for _ in range(W):
+        step()
+        B.tn_logz(ctx, Bn)
+    B.tn_ctx_profile(ctx)  # reset counters
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        if uuid and not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid if uuid else local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    times = []
+    for _ in range(K):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    launches = B.tn_ctx_profile(ctx)
+    gpu_launches = int(sum(v[0] for v in launches.values()))
+    logz, status = B.tn_logz(ctx, Bn)
+    total_ms = float(sum(times))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = Bn * world * K / (total_ms / 1e3)
+
+    # end to end through the host entry point (pinned host buffers)
+    pinned = torch.from_numpy(host).pin_memory()
+    hptrs = [pinned.data_ptr() + 8 * elems * i for i in range(Bn)]
+    for _ in range(W):
+        B.tn_contract_approx_host(ctx, plans, hptrs, prec, 0, sh)
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        lz_h, st_h = B.tn_contract_approx_host(ctx, plans, hptrs, prec, 0, sh)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": Bn * world * K / e2e_s, "unit": "contractions/s",
+           "h2d_bytes_per_step": int(8 * elems * Bn), "d2h_bytes_per_step": int(12 * Bn)}
+
+    # diagnostic pass: per-kernel-class durations (CUDA events), not timed above
+    B.tn_ctx_set_profiling(ctx, 1)
+    step()
+    prof = B.tn_ctx_profile(ctx)
+    B.tn_ctx_set_profiling(ctx, 0)
+    B.tn_logz(ctx, Bn)
+    flops = {"env": info["flops_env"], "local": info["flops_local"],
+             "density": info["flops_density"], "project": info["flops_project"],
+             "eig": info["flops_eig"]}
+    pk, pk_src = peaks()
+    dom = max(flops, key=lambda k: prof[k][1])
+    n_l, ms = prof[dom]
+    achieved = flops[dom] * Bn / (ms / 1e3) / 1e12
+    if prec == B.TN_PREC_FP64:
+        bound, peak, note = "alu", FP64_ALU_TFLOPS, "FP64 nominal 1.25 TFLOP/s (derived)"
+    elif dom == "eig":
+        bound, peak, note = "alu", FP32_ALU_TFLOPS, "FP32 152 SMs x 128 lanes x 2 x 2.07 GHz"
+    else:
+        bf16 = pk.get("bf16_tflops_sustained", FALLBACK["bf16_tflops_sustained"])
+        peak = bf16 * (TF32_PER_BF16 if prec == B.TN_PREC_TF32 else 1.0)
+        bound, note = "tensor", f"{pk_src} bf16 sustained" + (" x 1.1/2.25 (tf32)" if prec == B.TN_PREC_TF32 else "")
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            tr = json.load(f)
+        key = f"{args.precision}:{dom}"
+        if key in tr:
+            traffic = tr[key]
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel_class": dom,
+                "launches": n_l, "ms_per_batch": ms, "peak_source": note,
+                "class_ms": {k: round(v[1], 3) for k, v in prof.items()}}
+
+    out = {
+        "metric": "approx contractions/s", "value": value, "unit": "contractions/s",
+        "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": total_ms / K,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "tf32": "tf32", "bf16": "bf16"}[args.precision],
+        "data": "synthetic (seeded instances)",
+        "config": {"workload": WORKLOAD, "size": args.size, "chi": args.chi, "batch": Bn,
+                   "precision": args.precision, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"instances x{world}"},
+        "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline, "clocks": clocks,
+        "status_ok": int((status == 0).sum()),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        d = run_oracle(0, args.size, args.chi, args.cpu_seconds)
+        ref = np.asarray(d["logz"])
+        got = logz[:len(ref)]
+        out["cpu_baseline"] = {
+            "value": d["instances"] / d["seconds"], "unit": "contractions/s",
+            "cores": d["cores"], "kind": "oracle",
+            "sample": f"instances 0..{d['instances'] - 1} of this workload "
+                      f"({d['seconds']:.1f} s, FP64 numpy oracle, BLAS threads = cores)"}
+        out["parity"] = {"instances": len(ref),
+                         "max_rel_logz_err_vs_oracle": float(np.max(np.abs(got - ref) / np.abs(ref)))}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

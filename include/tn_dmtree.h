@@ -177,6 +177,31 @@ tn_status tn_contract_approx_host(tn_ctx_t* ctx, const tn_plan_t* const* plans, 
                                   int32_t learned_chi, double* logz_host,
                                   int32_t* status_host, void* stream);
 
+/* ------------------------------------------------------------- diagnostics
+ * Kernel classes of the hot path, for launch counts and timing.            */
+enum {
+  TN_KC_NORM = 0,     /* site-tensor normalisation                          */
+  TN_KC_FUSE = 1,     /* block fusion, contract T(v) first (Sec. 5.3)        */
+  TN_KC_ENV = 2,      /* root-side memoised density matrices (Eq. dm_cache) */
+  TN_KC_LOCAL = 3,    /* local blocks M_v                                    */
+  TN_KC_DENSITY = 4,  /* density matrices L_v = M_v L_u M_v^T                */
+  TN_KC_EIG = 5,      /* leading_eigenvectors                                */
+  TN_KC_PROJECT = 6,  /* projector application U_v^T M_v                     */
+  TN_KC_ROOT = 7,     /* root M_r and its normalisation                      */
+  TN_KC_CLOSE = 8,    /* closing contraction of the last partition           */
+  TN_KC_COUNT = 9
+};
+/* Turn per-launch CUDA-event timing on (1) or off (0) for later batches of
+ * ctx.  Launch counting is always on.  Timing adds two events per launch,
+ * so timed numbers of a batch run with profiling on are diagnostics only. */
+tn_status tn_ctx_set_profiling(tn_ctx_t* ctx, int32_t on);
+/* Per class (n_classes <= TN_KC_COUNT entries, host arrays): kernel
+ * launches and, when profiling was on, summed launch durations in ms
+ * (CUDA events on the launching stream), since the last call.  Waits for
+ * the ctx's stream, then resets the counters.  ms_host may be NULL.        */
+tn_status tn_ctx_profile(tn_ctx_t* ctx, double* ms_host, int64_t* launches_host,
+                         int32_t n_classes);
+
 /* One-line reason for the last non-OK status returned on this thread (ctx
  * may be NULL for calls that have none).  Valid until the next call.       */
 const char* tn_last_error(const tn_ctx_t* ctx);

@@ -55,7 +55,10 @@ _lib = None
 # Every symbol include/tn_dmtree.h declares.
 EXPORTS = ("tn_plan", "tn_plan_destroy", "tn_plan_query", "tn_plan_site_offset",
            "tn_ctx_create", "tn_ctx_destroy", "tn_embed_tree", "tn_contract_approx",
-           "tn_logz", "tn_contract_approx_host", "tn_last_error")
+           "tn_logz", "tn_contract_approx_host", "tn_ctx_set_profiling", "tn_ctx_profile",
+           "tn_last_error")
+
+KERNEL_CLASSES = ("norm", "fuse", "env", "local", "density", "eig", "project", "root", "close")
 
 
 def lib():
@@ -82,6 +85,9 @@ def lib():
     L.tn_contract_approx_host.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.c_int32,
                                           ctypes.POINTER(_vp), ctypes.c_int32, ctypes.c_int32,
                                           ctypes.POINTER(ctypes.c_double), _i32p, _vp]
+    L.tn_ctx_set_profiling.argtypes = [_vp, ctypes.c_int32]
+    L.tn_ctx_profile.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]
     L.tn_last_error.argtypes = [_vp]
     L.tn_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -238,6 +244,19 @@ def tn_contract_approx_host(ctx, plans, sites_host, precision=TN_PREC_FP64, lear
     if st != TN_OK and (raise_on_error or st not in (4, 5)):
         _check(st, ctx)
     return logz, status
+
+
+def tn_ctx_set_profiling(ctx, on):
+    _check(lib().tn_ctx_set_profiling(ctx.handle, int(bool(on))), ctx)
+
+
+def tn_ctx_profile(ctx):
+    """Returns {class: (launches, ms)} since the last call (ms = 0 unless profiling)."""
+    n = len(KERNEL_CLASSES)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int64 * n)()
+    _check(lib().tn_ctx_profile(ctx.handle, ms, cnt, n), ctx)
+    return {k: (int(cnt[i]), float(ms[i])) for i, k in enumerate(KERNEL_CLASSES)}
 
 
 def pack_sites(plan, tensors):

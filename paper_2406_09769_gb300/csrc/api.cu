@@ -77,6 +77,14 @@ struct tn_ctx {
   void* pinned = nullptr;
   size_t pinned_cap = 0;
   cudaEvent_t pinned_free = nullptr;
+  // diagnostics: launch counts per kernel class, optional event timing
+  bool prof = false;
+  int64_t launches[TN_KC_COUNT] = {};
+  struct Rec {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
   // device pointers carved from `results`
   double* logz = nullptr;
   int* status = nullptr;
@@ -151,6 +159,26 @@ void ensure_results(tn_ctx* c, int B) {
   c->logscale = reinterpret_cast<double*>(base + align256(sizeof(double) * B));
   c->status = reinterpret_cast<int*>(base + 2 * align256(sizeof(double) * B));
 }
+
+// Counts one launch of a kernel class and, when profiling, brackets it with
+// CUDA events on the launching stream.
+struct Scope {
+  tn_ctx* c;
+  int cls;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  Scope(tn_ctx* c_, int cls_, cudaStream_t s_) : c(c_), cls(cls_), s(s_) {
+    if (c->prof && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, s);
+  }
+  ~Scope() {
+    c->launches[cls]++;
+    cudaEvent_t b = nullptr;
+    if (a && cudaEventCreate(&b) == cudaSuccess) {
+      cudaEventRecord(b, s);
+      c->recs.push_back({cls, a, b});
+    }
+  }
+};
 
 void* pinned_get(tn_ctx* c, size_t bytes) {
   ck(cudaEventSynchronize(c->pinned_free), "cudaEventSynchronize");
@@ -230,10 +258,11 @@ std::vector<StepTables> upload_tables(tn_ctx* c, const tn_plan_t* P, const doubl
   return out;
 }
 
-void gemm(bool ta, bool tb, const double* A, long long sA, int lda, const double* Bm, long long sB,
-          int ldb, double* C, long long sC, int ldc, int M, int N, int K, int batch,
-          const unsigned long long* amax_in, long long s_in, unsigned long long* amax_out,
-          long long s_out, cudaStream_t st) {
+void gemm(tn_ctx* c, int cls, bool ta, bool tb, const double* A, long long sA, int lda,
+          const double* Bm, long long sB, int ldb, double* C, long long sC, int ldc, int M, int N,
+          int K, int batch, const unsigned long long* amax_in, long long s_in,
+          unsigned long long* amax_out, long long s_out, cudaStream_t st) {
+  Scope sc(c, cls, st);
   tn::GemmArgs g{};
   g.A = A; g.sA = sA; g.lda = lda;
   g.B = Bm; g.sB = sB; g.ldb = ldb;
@@ -257,16 +286,17 @@ void dm_pass(tn_ctx* c, const tn::Step& st, const Ws& w, double* Snext, int B, i
   // Each R_k is kept unnormalised; its running max-abs (amax[k]) scales the
   // GEMM that consumes it, which keeps every R within range.
   ck(cudaMemsetAsync(w.amax, 0, sizeof(unsigned long long) * w.sAmax * B, strm), "memset amax");
+  Scope(c, TN_KC_ENV, strm),
   ck(tn::launch_fill_env_root(w.R + st.r_off[n - 1], w.sR, w.amax + (n - 1), w.sAmax, B, strm),
      "env root");
   for (int k = n - 1; k >= 2; --k) {
     const double* Yk = w.Y + st.y_off[k];
     const int Dl = D[k - 1], Dr = D[k], dk = d[k];
     // X = Y_k (Dl*dk x Dr) . R_k / max|R_k|
-    gemm(false, false, Yk, w.sY, Dr, w.R + st.r_off[k], w.sR, Dr, w.X, w.sX, Dr, Dl * dk, Dr, Dr,
+    gemm(c, TN_KC_ENV, false, false, Yk, w.sY, Dr, w.R + st.r_off[k], w.sR, Dr, w.X, w.sX, Dr, Dl * dk, Dr, Dr,
          B, w.amax + k, w.sAmax, nullptr, 0, strm);
     // R_{k-1} = X (Dl x dk*Dr) . Y_k(Dl x dk*Dr)^T
-    gemm(false, true, w.X, w.sX, dk * Dr, Yk, w.sY, dk * Dr, w.R + st.r_off[k - 1], w.sR, Dl, Dl,
+    gemm(c, TN_KC_ENV, false, true, w.X, w.sX, dk * Dr, Yk, w.sY, dk * Dr, w.R + st.r_off[k - 1], w.sR, Dl, Dl,
          Dl, dk * Dr, B, nullptr, 0, w.amax + (k - 1), w.sAmax, strm);
   }
   // Post-order over the MPS tree: vertices 1 .. n-2.
@@ -276,23 +306,25 @@ void dm_pass(tn_ctx* c, const tn::Step& st, const Ws& w, double* Snext, int B, i
     const double* Pp = (k == 1) ? w.Y + st.y_off[0] : w.P;
     const long long sPp = (k == 1) ? w.sY : w.sP;
     // M_v = P_{v-1} . Y_v  -> (rp x dk*Dr) = (A x Dr)
-    gemm(false, false, Pp, sPp, Dl, w.Y + st.y_off[k], w.sY, dk * Dr, w.M, w.sM, dk * Dr, rp,
+    gemm(c, TN_KC_LOCAL, false, false, Pp, sPp, Dl, w.Y + st.y_off[k], w.sY, dk * Dr, w.M, w.sM, dk * Dr, rp,
          dk * Dr, Dl, B, nullptr, 0, nullptr, 0, strm);
     // L_v = M_v R_k M_v^T  (R_k scaled by 1/max|R_k|)
-    gemm(false, false, w.M, w.sM, Dr, w.R + st.r_off[k], w.sR, Dr, w.G, w.sM, Dr, A, Dr, Dr, B,
+    gemm(c, TN_KC_DENSITY, false, false, w.M, w.sM, Dr, w.R + st.r_off[k], w.sR, Dr, w.G, w.sM, Dr, A, Dr, Dr, B,
          w.amax + k, w.sAmax, nullptr, 0, strm);
-    gemm(false, true, w.G, w.sM, Dr, w.M, w.sM, Dr, w.L, w.sL, A, A, A, Dr, B, nullptr, 0, nullptr,
+    gemm(c, TN_KC_DENSITY, false, true, w.G, w.sM, Dr, w.M, w.sM, Dr, w.L, w.sL, A, A, A, Dr, B, nullptr, 0, nullptr,
          0, strm);
     // U_v = leading_eigenvectors(L_v, r_k), written as boundary site k
     double* Uk = Snext + st.s_off[k];
+    Scope(c, TN_KC_EIG, strm),
     ck(tn::launch_eigh_top<double>(w.L, w.sL, Uk, w.sS, w.lam, w.sLam, A, rk, 0, c->status, B,
                                    strm),
        "eigh launch");
     // P_v = U_v^T M_v  (rk x Dr)
-    gemm(true, false, Uk, w.sS, rk, w.M, w.sM, Dr, w.P, w.sP, Dr, rk, Dr, A, B, nullptr, 0,
+    gemm(c, TN_KC_PROJECT, true, false, Uk, w.sS, rk, w.M, w.sM, Dr, w.P, w.sP, Dr, rk, Dr, A, B, nullptr, 0,
          nullptr, 0, strm);
   }
   // Root: M_r = P_{n-2} . Y_{n-1}, scaled to unit norm into the log-scale.
+  Scope(c, TN_KC_ROOT, strm),
   ck(tn::launch_root(w.P, w.sP, w.Y + st.y_off[n - 1], w.sY, st.r[n - 2], D[n - 2], d[n - 1],
                      Snext + st.s_off[n - 1], Snext + st.s_off[0], d[0], w.sS, c->logscale,
                      c->status, B, strm),
@@ -310,6 +342,7 @@ void run_plan(tn_ctx* c, const tn_plan_t* P, int B, const double* const* tens_de
   int64_t *off_dev = nullptr, *len_dev = nullptr;
   std::vector<StepTables> tabs =
       upload_tables(c, P, tens_dev, B, &tens_table, &off_dev, &len_dev, strm);
+  Scope(c, TN_KC_NORM, strm),
   ck(tn::launch_site_norm(tens_table, off_dev, len_dev, P->n_vertices, B, w.inv, c->logscale,
                           c->status, strm),
      "site norm");
@@ -323,22 +356,26 @@ void run_plan(tn_ctx* c, const tn_plan_t* P, int B, const double* const* tens_de
       maxe = std::max<int>(maxe, o.a * o.dhl * o.de * o.b * o.dhr);
     }
     if (st.kind == 0) {
+      Scope(c, TN_KC_FUSE, strm),
       ck(tn::launch_fuse(tabs[s].fuse, st.n, maxe, tens_table, w.inv, P->n_vertices, nullptr, 0, 1,
                          Snext, w.sS, B, strm),
          "fuse");
       std::swap(Scur, Snext);
     } else if (st.kind == 1) {
+      Scope(c, TN_KC_FUSE, strm),
       ck(tn::launch_fuse(tabs[s].fuse, st.n, maxe, tens_table, w.inv, P->n_vertices, Scur, w.sS, 0,
                          w.Y, w.sY, B, strm),
          "fuse");
       dm_pass(c, st, w, Snext, B, precision, strm);
       std::swap(Scur, Snext);
     } else {
+      Scope(c, TN_KC_FUSE, strm),
       ck(tn::launch_fuse(tabs[s].fuse, st.n, maxe, tens_table, w.inv, P->n_vertices, Scur, w.sS, 0,
                          w.Y, w.sY, B, strm),
          "fuse");
       int maxD = 1;
       for (int k = 0; k < st.n; ++k) maxD = std::max(maxD, st.D[k]);
+      Scope(c, TN_KC_CLOSE, strm),
       ck(tn::launch_close(w.Y, w.sY, tabs[s].y_off, tabs[s].D, st.n, maxD, c->logscale, c->logz,
                           c->status, B, strm),
          "close");
@@ -598,6 +635,43 @@ extern "C" tn_status tn_embed_tree(tn_ctx_t* c, int32_t n_inst, int32_t n_legs,
                        strm),
        "copy status");
     for (int k = 0; k < n - 1; ++k) ranks_host[k] = st.r[k];
+  });
+}
+
+extern "C" tn_status tn_ctx_set_profiling(tn_ctx_t* c, int32_t on) {
+  if (!c) {
+    tn::set_error("tn_ctx_set_profiling: ctx is NULL");
+    return TN_ERR_INVALID;
+  }
+  c->prof = (on != 0);
+  return TN_OK;
+}
+
+extern "C" tn_status tn_ctx_profile(tn_ctx_t* c, double* ms_host, int64_t* launches_host,
+                                    int32_t n_classes) {
+  if (!c) {
+    tn::set_error("tn_ctx_profile: ctx is NULL");
+    return TN_ERR_INVALID;
+  }
+  return guarded(c, "tn_ctx_profile", [&] {
+    if (n_classes < 0 || n_classes > TN_KC_COUNT || !launches_host)
+      fail(TN_ERR_INVALID, "invalid argument");
+    ck(cudaSetDevice(c->device), "cudaSetDevice");
+    ck(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    double ms[TN_KC_COUNT] = {};
+    for (const auto& r : c->recs) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) ms[r.cls] += t;
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    cudaGetLastError();
+    c->recs.clear();
+    for (int k = 0; k < n_classes; ++k) {
+      launches_host[k] = c->launches[k];
+      if (ms_host) ms_host[k] = ms[k];
+    }
+    for (int k = 0; k < TN_KC_COUNT; ++k) c->launches[k] = 0;
   });
 }
 

@@ -359,17 +359,42 @@ cudaError_t launch_eigh_top(const T* L, long long sL, double* U, long long sU, d
                             cudaStream_t st) {
   if (n < 1 || n > kNmax || r < 1 || r > n || nlam > n) return cudaErrorInvalidValue;
   const size_t smem = eigh_smem_bytes<T>(n, r, nlam);
-  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  if (smem > eigh_smem_limit<T>()) return cudaErrorInvalidValue;
   k_eigh_top<T><<<batch, kThreads, smem, st>>>(L, sL, U, sU, lam, slam, n, r, nlam, status);
   return cudaGetLastError();
 }
 
-cudaError_t eigh_configure() {
-  cudaError_t e = cudaFuncSetAttribute(k_eigh_top<double>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+namespace {
+size_t g_limit[2] = {0, 0};
+
+template <typename T>
+cudaError_t configure_one(int slot) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_eigh_top<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              227 * 1024);
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa{};
+  e = cudaFuncGetAttributes(&fa, k_eigh_top<T>);
+  if (e != cudaSuccess) return e;
+  const size_t lim = size_t(optin) - fa.sharedSizeBytes;
+  e = cudaFuncSetAttribute(k_eigh_top<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(lim));
+  if (e == cudaSuccess) g_limit[slot] = lim;
+  return e;
+}
+}  // namespace
+
+template <typename T>
+size_t eigh_smem_limit() {
+  return g_limit[sizeof(T) == 8 ? 0 : 1];
+}
+template size_t eigh_smem_limit<double>();
+template size_t eigh_smem_limit<float>();
+
+cudaError_t eigh_configure() {
+  cudaError_t e = configure_one<double>(0);
+  if (e != cudaSuccess) return e;
+  return configure_one<float>(1);
 }
 
 template size_t eigh_smem_bytes<double>(int, int, int);

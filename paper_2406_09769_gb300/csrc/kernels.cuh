@@ -58,6 +58,8 @@ cudaError_t launch_eigh_top(const T* L, long long sL, double* U, long long sU, d
                             cudaStream_t st);
 template <typename T>
 size_t eigh_smem_bytes(int n, int r, int nlam);
+template <typename T>
+size_t eigh_smem_limit();
 cudaError_t eigh_configure();
 
 }  // namespace tn

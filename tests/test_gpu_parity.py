@@ -70,10 +70,12 @@ def test_embed_tree_matches_oracle(ctx, d, D, chi):
     n_inst = 3
     chains = [_random_chain(100 + i, d, D) for i in range(n_inst)]
     dev_in = [torch.from_numpy(np.concatenate([b.reshape(-1) for b in ch])).cuda() for ch in chains]
-    ref = []
+    ref, traces = [], []
     for ch in chains:
         blocks = [None, np.einsum("xeb,bfc->efc", ch[0], ch[1])] + ch[2:]
-        ref.append(dmtree.density_matrix_alg(blocks, chi))
+        tr = []
+        ref.append(dmtree.density_matrix_alg(blocks, chi, trace=tr))
+        traces.append(tr)
     r = [d[0]]
     for k in range(1, n - 1):
         r.append(min(chi, r[-1] * d[k], D[k], int(np.prod(d[k + 1:]))))
@@ -93,13 +95,29 @@ def test_embed_tree_matches_oracle(ctx, d, D, chi):
         U_ref, Mr_ref, ln_ref = ref[i]
         got = outs[i].cpu().numpy()
         pos = 0
+        compared = 0
         for v in range(1, n - 1):
             Ug = got[pos:pos + sizes[v - 1]].reshape(U_ref[v].shape)
             pos += sizes[v - 1]
-            np.testing.assert_allclose(Ug, U_ref[v], atol=1e-9)
             np.testing.assert_allclose(Ug.T @ Ug, np.eye(Ug.shape[1]), atol=1e-12)
+            # An eigenvector is determined to ~eps ||L|| / gap (absolute
+            # accuracy of any backward-stable solver): compare each column
+            # with that bound, and the kept subspace when its gap is clear.
+            lam = traces[i][v - 1]["lam"]
+            rk = Ug.shape[1]
+            for j in range(rk):
+                gaps = [abs(lam[j] - lam[k]) for k in (j - 1, j + 1) if 0 <= k < len(lam)]
+                relgap = (min(gaps) if gaps else lam[0]) / lam[0]
+                if relgap > 1e-6:
+                    np.testing.assert_allclose(Ug[:, j], U_ref[v][:, j],
+                                               atol=1e-9 + 1e-13 / relgap)
+                    compared += 1
+            if rk < len(lam) and (lam[rk - 1] - lam[rk]) / lam[0] > 1e-8:
+                np.testing.assert_allclose(Ug @ Ug.T, U_ref[v] @ U_ref[v].T, atol=1e-8)
+        assert compared >= n - 2
         Mg = got[pos:].reshape(Mr_ref.shape)
-        np.testing.assert_allclose(Mg, Mr_ref, atol=1e-9)
+        # gauge-invariant on the root's tree bond
+        np.testing.assert_allclose(Mg.T @ Mg, Mr_ref.T @ Mr_ref, atol=1e-9)
         assert lognorm[i].item() == pytest.approx(ln_ref, abs=1e-11)
 
 
