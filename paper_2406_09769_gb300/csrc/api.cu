@@ -85,10 +85,12 @@ struct tn_ctx {
     cudaEvent_t a, b;
   };
   std::vector<Rec> recs;
+  bool tc_ready = false;  // tcgen05/TMA path configured on this device
   // device pointers carved from `results`
   double* logz = nullptr;
   int* status = nullptr;
   double* logscale = nullptr;
+  int* err_flag = nullptr;  // set by a kernel whose bounded wait expired
 };
 
 namespace {
@@ -154,10 +156,61 @@ Ws carve(tn_ctx* c, const Dims& d, int B, int nv) {
 
 void ensure_results(tn_ctx* c, int B) {
   char* base = static_cast<char*>(c->results.get(align256(sizeof(double) * B) * 2 +
-                                                 align256(sizeof(int) * B)));
+                                                 align256(sizeof(int) * B) + 256));
   c->logz = reinterpret_cast<double*>(base);
   c->logscale = reinterpret_cast<double*>(base + align256(sizeof(double) * B));
   c->status = reinterpret_cast<int*>(base + 2 * align256(sizeof(double) * B));
+  c->err_flag = reinterpret_cast<int*>(base + 2 * align256(sizeof(double) * B) +
+                                       align256(sizeof(int) * B));
+}
+
+// Per-step buffer offsets (elements) of one executor.
+struct Lay {
+  std::vector<int64_t> y_off, s_off, r_off;
+  int64_t y_total = 0, s_total = 0, r_total = 0;
+};
+
+Lay lay_fp64(const tn::Step& st) {
+  Lay l;
+  l.y_off = st.y_off;
+  l.s_off = st.s_off;
+  l.r_off = st.r_off;
+  l.y_total = st.y_total;
+  l.s_total = st.s_total;
+  l.r_total = st.r_total;
+  return l;
+}
+
+int64_t up4(int64_t x) { return (x + 3) & ~int64_t(3); }
+
+// 16-byte aligned FP32 offsets (TMA needs 16-byte aligned bases and strides).
+Lay lay_f32(const tn::Step& st) {
+  Lay l;
+  const int n = st.n;
+  l.y_off.assign(n, 0);
+  l.s_off.assign(n, 0);
+  l.r_off.assign(n, 0);
+  int64_t off = 0;
+  for (int k = 0; k < n; ++k) {
+    const tn::SiteOp& o = st.site[k];
+    l.y_off[k] = off;
+    off += up4(int64_t(o.a) * o.dhl * o.de * o.b * o.dhr);
+  }
+  l.y_total = off;
+  off = 0;
+  for (int k = 0; k < n; ++k) {
+    l.s_off[k] = off;
+    off += up4(st.s_size[k]);
+  }
+  l.s_total = off;
+  off = 0;
+  if (st.kind == 1)
+    for (int k = 1; k <= n - 1; ++k) {
+      l.r_off[k] = off;
+      off += up4(int64_t(st.D[k]) * st.D[k]);
+    }
+  l.r_total = off;
+  return l;
 }
 
 // Counts one launch of a kernel class and, when profiling, brackets it with
@@ -202,8 +255,9 @@ struct StepTables {
   int32_t* D;  // n + 1 entries (last = max D)
 };
 
-std::vector<StepTables> upload_tables(tn_ctx* c, const tn_plan_t* P, const double* const* tens_dev,
-                                      int B, const double*** tens_table, int64_t** off_dev,
+std::vector<StepTables> upload_tables(tn_ctx* c, const tn_plan_t* P, const std::vector<Lay>& lay,
+                                      const double* const* tens_dev, int B,
+                                      const double*** tens_table, int64_t** off_dev,
                                       int64_t** len_dev, cudaStream_t st) {
   // layout: [tens ptrs B][site_off nv][site_len nv] then per step fuse/y_off/D
   const int nv = P->n_vertices;
@@ -238,12 +292,12 @@ std::vector<StepTables> upload_tables(tn_ctx* c, const tn_plan_t* P, const doubl
       f.vertex = op.vertex; f.a = op.a; f.dp = op.dp; f.b = op.b;
       f.dhl = op.dhl; f.dhr = op.dhr; f.de = op.de;
       f.t_off = op.t_off; f.sp = op.sp; f.shl = op.shl; f.shr = op.shr; f.se = op.se;
-      f.y_off = (stp.kind == 0) ? stp.s_off[k] : stp.y_off[k];
-      f.s_off = (s > 0) ? P->steps[s - 1].s_off[k] : 0;
+      f.y_off = (stp.kind == 0) ? lay[s].s_off[k] : lay[s].y_off[k];
+      f.s_off = (s > 0) ? lay[s - 1].s_off[k] : 0;
       fh[k] = f;
     }
     q += align256(sizeof(tn::FuseSite) * n);
-    std::memcpy(h + q, stp.y_off.data(), sizeof(int64_t) * n);
+    std::memcpy(h + q, lay[s].y_off.data(), sizeof(int64_t) * n);
     out[s].y_off = reinterpret_cast<int64_t*>(dbase + q);
     q += align256(sizeof(int64_t) * n);
     std::vector<int32_t> D(stp.D);
@@ -316,8 +370,8 @@ void dm_pass(tn_ctx* c, const tn::Step& st, const Ws& w, double* Snext, int B, i
     // U_v = leading_eigenvectors(L_v, r_k), written as boundary site k
     double* Uk = Snext + st.s_off[k];
     Scope(c, TN_KC_EIG, strm),
-    ck(tn::launch_eigh_top<double>(w.L, w.sL, Uk, w.sS, w.lam, w.sLam, A, rk, 0, c->status, B,
-                                   strm),
+    ck(tn::launch_eigh_top<double>(w.L, w.sL, Uk, w.sS, nullptr, 0, w.lam, w.sLam, A, rk, 0,
+                                   c->status, B, strm),
        "eigh launch");
     // P_v = U_v^T M_v  (rk x Dr)
     gemm(c, TN_KC_PROJECT, true, false, Uk, w.sS, rk, w.M, w.sM, Dr, w.P, w.sP, Dr, rk, Dr, A, B, nullptr, 0,
@@ -333,15 +387,16 @@ void dm_pass(tn_ctx* c, const tn::Step& st, const Ws& w, double* Snext, int B, i
 
 void run_plan(tn_ctx* c, const tn_plan_t* P, int B, const double* const* tens_dev, int precision,
               cudaStream_t strm) {
-  if (precision != TN_PREC_FP64)
-    fail(TN_ERR_UNSUPPORTED, "this build runs the FP64 path only (precision 0)");
   const Dims dm = plan_dims(P);
   ensure_results(c, B);
+  ck(cudaMemsetAsync(c->err_flag, 0, sizeof(int), strm), "memset err");
   const Ws w = carve(c, dm, B, P->n_vertices);
   const double** tens_table = nullptr;
   int64_t *off_dev = nullptr, *len_dev = nullptr;
+  std::vector<Lay> lay;
+  for (const tn::Step& st : P->steps) lay.push_back(lay_fp64(st));
   std::vector<StepTables> tabs =
-      upload_tables(c, P, tens_dev, B, &tens_table, &off_dev, &len_dev, strm);
+      upload_tables(c, P, lay, tens_dev, B, &tens_table, &off_dev, &len_dev, strm);
   Scope(c, TN_KC_NORM, strm),
   ck(tn::launch_site_norm(tens_table, off_dev, len_dev, P->n_vertices, B, w.inv, c->logscale,
                           c->status, strm),
@@ -378,6 +433,196 @@ void run_plan(tn_ctx* c, const tn_plan_t* P, int B, const double* const* tens_de
       Scope(c, TN_KC_CLOSE, strm),
       ck(tn::launch_close(w.Y, w.sY, tabs[s].y_off, tabs[s].D, st.n, maxD, c->logscale, c->logz,
                           c->status, B, strm),
+         "close");
+    }
+  }
+  c->stream = strm;
+  c->last_batch = B;
+  c->pending = true;
+}
+
+// ------------------------------------------------------ mixed precision path
+// FP32 storage; density-matrix contractions (env, L_v) as TF32 tensor-core
+// products with FP32 accumulation; the value path (M_v, P_v) with the
+// compensated 3-term TF32 split; FP32 eigensolver; root norm, log-scale and
+// closing contraction accumulated in FP64.
+struct WsF {
+  long long sS, sY, sR, sX, sM, sL, sP, sUt, sLam, sAmax, sInv;
+  float *S0, *S1, *Y, *Yt, *R, *X, *M, *Mt, *G, *L, *P, *Ut;
+  double *lam, *inv;
+  unsigned int* amax;
+};
+
+WsF carve_f32(tn_ctx* c, const tn_plan_t* P, const std::vector<Lay>& lay, int B) {
+  long long maxS = 4, maxY = 4, maxR = 4, maxX = 4, maxM = 4, maxL = 4, maxP = 4, maxUt = 4,
+            maxLam = 1;
+  int maxN = 1;
+  for (size_t s = 0; s < P->steps.size(); ++s) {
+    const tn::Step& st = P->steps[s];
+    maxS = std::max<long long>(maxS, lay[s].s_total);
+    maxY = std::max<long long>(maxY, lay[s].y_total);
+    maxR = std::max<long long>(maxR, lay[s].r_total);
+    maxN = std::max(maxN, st.n);
+    for (int k = 0; k < st.n; ++k) {
+      const tn::SiteOp& o = st.site[k];
+      maxX = std::max<long long>(maxX, up4((long long)o.a * o.dhl * o.de * o.b * o.dhr));
+    }
+    if (st.kind != 1) continue;
+    for (int k = 1; k <= st.n - 2; ++k) {
+      const long long A = (long long)st.r[k - 1] * st.d[k];
+      maxM = std::max<long long>(maxM, up4(A * st.D[k]));
+      maxL = std::max<long long>(maxL, up4(A * A));
+      maxP = std::max<long long>(maxP, up4((long long)st.r[k] * st.D[k]));
+      maxUt = std::max<long long>(maxUt, up4((long long)st.r[k] * A));
+      maxLam = std::max<long long>(maxLam, A);
+    }
+  }
+  WsF w{};
+  w.sS = maxS; w.sY = maxY; w.sR = maxR; w.sX = maxX; w.sM = maxM; w.sL = maxL; w.sP = maxP;
+  w.sUt = maxUt; w.sLam = maxLam; w.sAmax = maxN; w.sInv = P->n_vertices;
+  const long long fsz[] = {w.sS, w.sS, w.sY, w.sY, w.sR, w.sX, w.sM, w.sM, w.sM, w.sL, w.sP, w.sUt};
+  float** fout[] = {&w.S0, &w.S1, &w.Y, &w.Yt, &w.R, &w.X, &w.M, &w.Mt, &w.G, &w.L, &w.P, &w.Ut};
+  size_t off[16], tot = 0;
+  for (int i = 0; i < 12; ++i) {
+    off[i] = tot;
+    tot += align256(sizeof(float) * size_t(fsz[i]) * B);
+  }
+  off[12] = tot;
+  tot += align256(sizeof(double) * size_t(w.sLam) * B);
+  off[13] = tot;
+  tot += align256(sizeof(double) * size_t(w.sInv) * B);
+  off[14] = tot;
+  tot += align256(sizeof(unsigned int) * size_t(w.sAmax) * B);
+  char* base = static_cast<char*>(c->arena.get(tot));
+  for (int i = 0; i < 12; ++i) *fout[i] = reinterpret_cast<float*>(base + off[i]);
+  w.lam = reinterpret_cast<double*>(base + off[12]);
+  w.inv = reinterpret_cast<double*>(base + off[13]);
+  w.amax = reinterpret_cast<unsigned int*>(base + off[14]);
+  return w;
+}
+
+// C_i = alpha_i A_i B_i^T on the tensor cores when TMA can address the operands
+// (16-byte aligned bases and leading dimensions), else the SIMT fallback.
+void tgemm(tn_ctx* c, int cls, const float* A, long long sA, int lda, const float* Bm,
+           long long sB, int ldb, float* C, long long sC, int ldc, float* Ct, long long sCt,
+           int ldct, int ct_cols, int M, int N, int K, int batch, const unsigned int* amax_in,
+           long long s_in, unsigned int* amax_out, long long s_out, int split, cudaStream_t st) {
+  Scope sc(c, cls, st);
+  tn::TcGemmArgs g{};
+  g.A = A; g.sA = sA; g.lda = lda;
+  g.B = Bm; g.sB = sB; g.ldb = ldb;
+  g.C = C; g.sC = sC; g.ldc = ldc;
+  g.Ct = Ct; g.sCt = sCt; g.ldct = ldct; g.ct_cols = ct_cols > 0 ? ct_cols : N;
+  g.M = M; g.N = N; g.K = K; g.batch = batch;
+  g.amax_in = amax_in; g.s_amax_in = s_in;
+  g.amax_out = amax_out; g.s_amax_out = s_out;
+  g.split = split;
+  g.err = c->err_flag;
+  const bool aligned = (lda % 4 == 0) && (ldb % 4 == 0) && (sA % 4 == 0) && (sB % 4 == 0) &&
+                       (reinterpret_cast<uintptr_t>(A) % 16 == 0) &&
+                       (reinterpret_cast<uintptr_t>(Bm) % 16 == 0);
+  if (aligned && c->tc_ready) {
+    ck(tn::launch_tc_gemm(g, st), "tcgen05 gemm launch");
+  } else {
+    ck(tn::launch_sgemm_nt(g, st), "sgemm launch");
+  }
+}
+
+void dm_pass_tc(tn_ctx* c, const tn::Step& st, const Lay& l, const WsF& w, float* Snext, int B,
+                cudaStream_t strm) {
+  const int n = st.n;
+  const auto& D = st.D;
+  const auto& d = st.d;
+  ck(cudaMemsetAsync(w.amax, 0, sizeof(unsigned int) * w.sAmax * B, strm), "memset amax");
+  Scope(c, TN_KC_ENV, strm),
+  ck(tn::launch_fill_env_root_f32(w.R + l.r_off[n - 1], w.sR, w.amax + (n - 1), w.sAmax, B, strm),
+     "env root");
+  // Memoised root-side density matrices, Eq. (dm_cache) (subspace path, TF32).
+  // B = R_k enters as its own transpose: R_k is symmetric.
+  for (int k = n - 1; k >= 2; --k) {
+    const float* Yk = w.Y + l.y_off[k];
+    const int Dl = D[k - 1], Dr = D[k], dk = d[k];
+    tgemm(c, TN_KC_ENV, Yk, w.sY, Dr, w.R + l.r_off[k], w.sR, Dr, w.X, w.sX, Dr, nullptr, 0, 0, 0,
+          Dl * dk, Dr, Dr, B, w.amax + k, w.sAmax, nullptr, 0, 0, strm);
+    tgemm(c, TN_KC_ENV, w.X, w.sX, dk * Dr, Yk, w.sY, dk * Dr, w.R + l.r_off[k - 1], w.sR, Dl,
+          nullptr, 0, 0, 0, Dl, Dl, dk * Dr, B, nullptr, 0, w.amax + (k - 1), w.sAmax, 0, strm);
+  }
+  for (int k = 1; k <= n - 2; ++k) {
+    const int rp = st.r[k - 1], rk = st.r[k], dk = d[k], Dl = D[k - 1], Dr = D[k];
+    const int A = rp * dk;
+    const float* Pp = (k == 1) ? w.Y + l.y_off[0] : w.P;
+    const long long sPp = (k == 1) ? w.sY : w.sP;
+    // M_v = P_{v-1} Y_v (value path, compensated); also M_v^T for the projector.
+    tgemm(c, TN_KC_LOCAL, Pp, sPp, Dl, w.Yt + l.y_off[k], w.sY, Dl, w.M, w.sM, dk * Dr, w.Mt,
+          w.sM, A, Dr, rp, dk * Dr, Dl, B, nullptr, 0, nullptr, 0, 1, strm);
+    // L_v = M_v R_k M_v^T (subspace path)
+    tgemm(c, TN_KC_DENSITY, w.M, w.sM, Dr, w.R + l.r_off[k], w.sR, Dr, w.G, w.sM, Dr, nullptr, 0, 0,
+          0, A, Dr, Dr, B, w.amax + k, w.sAmax, nullptr, 0, 0, strm);
+    tgemm(c, TN_KC_DENSITY, w.G, w.sM, Dr, w.M, w.sM, Dr, w.L, w.sL, A, nullptr, 0, 0, 0, A, A, Dr,
+          B, nullptr, 0, nullptr, 0, 0, strm);
+    float* Uk = Snext + l.s_off[k];
+    Scope(c, TN_KC_EIG, strm),
+    ck(tn::launch_eigh_top<float>(w.L, w.sL, Uk, w.sS, w.Ut, w.sUt, w.lam, w.sLam, A, rk, 0,
+                                  c->status, B, strm),
+       "eigh launch");
+    // P_v = U_v^T M_v (value path, compensated)
+    tgemm(c, TN_KC_PROJECT, w.Ut, w.sUt, A, w.Mt, w.sM, A, w.P, w.sP, Dr, nullptr, 0, 0, 0, rk,
+          Dr, A, B, nullptr, 0, nullptr, 0, 1, strm);
+  }
+  Scope(c, TN_KC_ROOT, strm),
+  ck(tn::launch_root_f32(w.P, w.sP, D[n - 2], w.Y + l.y_off[n - 1], w.sY, st.r[n - 2], D[n - 2],
+                         d[n - 1], Snext + l.s_off[n - 1], Snext + l.s_off[0], d[0], w.sS,
+                         c->logscale, c->status, B, strm),
+     "root launch");
+}
+
+void run_plan_tc(tn_ctx* c, const tn_plan_t* P, int B, const double* const* tens_dev,
+                 cudaStream_t strm) {
+  std::vector<Lay> lay;
+  for (const tn::Step& st : P->steps) lay.push_back(lay_f32(st));
+  ensure_results(c, B);
+  ck(cudaMemsetAsync(c->err_flag, 0, sizeof(int), strm), "memset err");
+  const WsF w = carve_f32(c, P, lay, B);
+  const double** tens_table = nullptr;
+  int64_t *off_dev = nullptr, *len_dev = nullptr;
+  std::vector<StepTables> tabs =
+      upload_tables(c, P, lay, tens_dev, B, &tens_table, &off_dev, &len_dev, strm);
+  Scope(c, TN_KC_NORM, strm),
+  ck(tn::launch_site_norm(tens_table, off_dev, len_dev, P->n_vertices, B, w.inv, c->logscale,
+                          c->status, strm),
+     "site norm");
+  float* Scur = w.S0;
+  float* Snext = w.S1;
+  for (size_t s = 0; s < P->steps.size(); ++s) {
+    const tn::Step& st = P->steps[s];
+    int maxe = 1;
+    for (int k = 0; k < st.n; ++k) {
+      const tn::SiteOp& o = st.site[k];
+      maxe = std::max<int>(maxe, o.a * o.dhl * o.de * o.b * o.dhr);
+    }
+    if (st.kind == 0) {
+      Scope(c, TN_KC_FUSE, strm),
+      ck(tn::launch_fuse_f32(tabs[s].fuse, st.n, maxe, tens_table, w.inv, P->n_vertices, nullptr,
+                             0, 1, Snext, w.sS, nullptr, nullptr, B, strm),
+         "fuse");
+      std::swap(Scur, Snext);
+    } else if (st.kind == 1) {
+      Scope(c, TN_KC_FUSE, strm),
+      ck(tn::launch_fuse_f32(tabs[s].fuse, st.n, maxe, tens_table, w.inv, P->n_vertices, Scur,
+                             w.sS, 0, w.Y, w.sY, w.Yt, tabs[s].y_off, B, strm),
+         "fuse");
+      dm_pass_tc(c, st, lay[s], w, Snext, B, strm);
+      std::swap(Scur, Snext);
+    } else {
+      Scope(c, TN_KC_FUSE, strm),
+      ck(tn::launch_fuse_f32(tabs[s].fuse, st.n, maxe, tens_table, w.inv, P->n_vertices, Scur,
+                             w.sS, 0, w.Y, w.sY, nullptr, nullptr, B, strm),
+         "fuse");
+      int maxD = 1;
+      for (int k = 0; k < st.n; ++k) maxD = std::max(maxD, st.D[k]);
+      Scope(c, TN_KC_CLOSE, strm),
+      ck(tn::launch_close_f32(w.Y, w.sY, tabs[s].y_off, tabs[s].D, st.n, maxD, c->logscale,
+                              c->logz, c->status, B, strm),
          "close");
     }
   }
@@ -430,6 +675,11 @@ extern "C" tn_status tn_ctx_create(int32_t device, tn_ctx_t** out) {
     c->device = device;
     ck(cudaEventCreateWithFlags(&c->pinned_free, cudaEventDisableTiming), "cudaEventCreate");
     ck(tn::eigh_configure(), "eigh configure");
+    int major = 0, minor = 0;
+    ck(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device), "attribute");
+    ck(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device), "attribute");
+    c->tc_ready = (major == 10 && minor == 3) && tn::tc_gemm_configure() == cudaSuccess;
+    cudaGetLastError();
   });
   if (s != TN_OK) {
     delete c;
@@ -469,7 +719,15 @@ extern "C" tn_status tn_contract_approx(tn_ctx_t* c, const tn_plan_t* const* pla
         fail(TN_ERR_UNSUPPORTED, "instances of one batch must share the plan structure");
     }
     ck(cudaSetDevice(c->device), "cudaSetDevice");
-    run_plan(c, plans[0], n_inst, sites_dev, precision, static_cast<cudaStream_t>(stream));
+    cudaStream_t strm = static_cast<cudaStream_t>(stream);
+    if (precision == TN_PREC_FP64) {
+      run_plan(c, plans[0], n_inst, sites_dev, precision, strm);
+    } else if (precision == TN_PREC_TF32) {
+      if (!c->tc_ready) fail(TN_ERR_UNSUPPORTED, "tcgen05 path unavailable on this device");
+      run_plan_tc(c, plans[0], n_inst, sites_dev, strm);
+    } else {
+      fail(TN_ERR_UNSUPPORTED, "precision mode not implemented in this build");
+    }
   });
 }
 
@@ -490,7 +748,16 @@ extern "C" tn_status tn_logz(tn_ctx_t* c, double* logz_host, int32_t* status_hos
     ck(cudaMemcpyAsync(status_host, c->status, sizeof(int) * n_inst, cudaMemcpyDeviceToHost,
                        c->stream),
        "copy status");
+    int err = 0;
+    ck(cudaMemcpyAsync(&err, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+       "copy err");
     ck(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    if (err) {
+      for (int i = 0; i < n_inst; ++i) {
+        status_host[i] = TN_ERR_TIMEOUT;
+        logz_host[i] = NAN;
+      }
+    }
     for (int i = 0; i < n_inst; ++i)
       if (status_host[i] != TN_OK && first == TN_OK) first = tn_status(status_host[i]);
     if (first != TN_OK) {

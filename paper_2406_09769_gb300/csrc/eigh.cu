@@ -73,9 +73,10 @@ __device__ int sturm_count(const T* dd, const T* e2, int n, T x, T pivmin) {
   return c;
 }
 
-template <typename T>
+template <typename T, typename TU>
 __global__ void __launch_bounds__(kThreads) k_eigh_top(const T* __restrict__ Lg, long long sL,
-                                                       double* __restrict__ Ug, long long sU,
+                                                       TU* __restrict__ Ug, long long sU,
+                                                       TU* __restrict__ Utg, long long sUt,
                                                        double* __restrict__ lamg, long long slam,
                                                        int n, int r, int nlam, int* status) {
   extern __shared__ __align__(16) unsigned char raw[];
@@ -106,8 +107,10 @@ __global__ void __launch_bounds__(kThreads) k_eigh_top(const T* __restrict__ Lg,
     A[a * ld + c] = x;
   }
   if (__syncthreads_or(bad)) {
-    double* U = Ug + (long long)b * sU;
-    for (int idx = tid; idx < n * r; idx += kThreads) U[idx] = 0.0;
+    TU* U = Ug + (long long)b * sU;
+    for (int idx = tid; idx < n * r; idx += kThreads) U[idx] = TU(0);
+    if (Utg)
+      for (int idx = tid; idx < n * r; idx += kThreads) Utg[(long long)b * sUt + idx] = TU(0);
     if (tid == 0) status[b] = TN_ERR_NONFINITE;
     return;
   }
@@ -334,10 +337,14 @@ __global__ void __launch_bounds__(kThreads) k_eigh_top(const T* __restrict__ Lg,
     for (int a = lane; a < n; a += 32) zc[a] *= sgn;
   }
   __syncthreads();
-  double* U = Ug + (long long)b * sU;
+  TU* U = Ug + (long long)b * sU;
   for (int idx = tid; idx < n * r; idx += kThreads) {
     const int a = idx / r, c = idx % r;
-    U[idx] = double(Z[c * n + a]);
+    U[idx] = TU(Z[c * n + a]);
+  }
+  if (Utg) {
+    TU* Ut = Utg + (long long)b * sUt;
+    for (int idx = tid; idx < n * r; idx += kThreads) Ut[idx] = TU(Z[idx]);
   }
   if (lamg) {
     double* lo = lamg + (long long)b * slam;
@@ -354,13 +361,14 @@ size_t eigh_smem_bytes(int n, int r, int nlam) {
 }
 
 template <typename T>
-cudaError_t launch_eigh_top(const T* L, long long sL, double* U, long long sU, double* lam,
-                            long long slam, int n, int r, int nlam, int* status, int batch,
-                            cudaStream_t st) {
+cudaError_t launch_eigh_top(const T* L, long long sL, T* U, long long sU, T* Ut, long long sUt,
+                            double* lam, long long slam, int n, int r, int nlam, int* status,
+                            int batch, cudaStream_t st) {
   if (n < 1 || n > kNmax || r < 1 || r > n || nlam > n) return cudaErrorInvalidValue;
   const size_t smem = eigh_smem_bytes<T>(n, r, nlam);
   if (smem > eigh_smem_limit<T>()) return cudaErrorInvalidValue;
-  k_eigh_top<T><<<batch, kThreads, smem, st>>>(L, sL, U, sU, lam, slam, n, r, nlam, status);
+  k_eigh_top<T, T><<<batch, kThreads, smem, st>>>(L, sL, U, sU, Ut, sUt, lam, slam, n, r, nlam,
+                                                  status);
   return cudaGetLastError();
 }
 
@@ -375,10 +383,11 @@ cudaError_t configure_one(int slot) {
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
   cudaFuncAttributes fa{};
-  e = cudaFuncGetAttributes(&fa, k_eigh_top<T>);
+  e = cudaFuncGetAttributes(&fa, k_eigh_top<T, T>);
   if (e != cudaSuccess) return e;
   const size_t lim = size_t(optin) - fa.sharedSizeBytes;
-  e = cudaFuncSetAttribute(k_eigh_top<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(lim));
+  e = cudaFuncSetAttribute(k_eigh_top<T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(lim));
   if (e == cudaSuccess) g_limit[slot] = lim;
   return e;
 }
@@ -400,8 +409,10 @@ cudaError_t eigh_configure() {
 template size_t eigh_smem_bytes<double>(int, int, int);
 template size_t eigh_smem_bytes<float>(int, int, int);
 template cudaError_t launch_eigh_top<double>(const double*, long long, double*, long long, double*,
-                                             long long, int, int, int, int*, int, cudaStream_t);
-template cudaError_t launch_eigh_top<float>(const float*, long long, double*, long long, double*,
-                                            long long, int, int, int, int*, int, cudaStream_t);
+                                             long long, double*, long long, int, int, int, int*,
+                                             int, cudaStream_t);
+template cudaError_t launch_eigh_top<float>(const float*, long long, float*, long long, float*,
+                                            long long, double*, long long, int, int, int, int*,
+                                            int, cudaStream_t);
 
 }  // namespace tn

@@ -30,6 +30,31 @@ struct GemmArgs {
 
 cudaError_t launch_dgemm(bool ta, bool tb, const GemmArgs& g, cudaStream_t st);
 
+// Batched tcgen05 contraction C_i = alpha_i * A_i B_i^T with FP32 operands,
+// TF32 tensor-core products and FP32 accumulation (K-major A: M x K, B: N x K).
+// lda, ldb, sA, sB must be multiples of 4 elements and A, B 16-byte aligned.
+// C (row-major, ldc) and/or Ct (= C^T, row-major, ldct) may be NULL.  alpha_i =
+// 1 / amax_in[i * s_amax_in] (float bits) when amax_in is set.  amax_out gets
+// max |C_i| (float bits, atomicMax; zero it first).  split = 1 adds the two
+// cross terms of a hi/lo TF32 split (compensated, ~FP32 accurate).  *err is
+// set to 1 if a bounded wait expired.
+struct TcGemmArgs {
+  const float* A; long long sA; int lda;
+  const float* B; long long sB; int ldb;
+  float* C; long long sC; int ldc;
+  float* Ct; long long sCt; int ldct;
+  int M, N, K, batch;
+  const unsigned int* amax_in; long long s_amax_in;
+  unsigned int* amax_out; long long s_amax_out;
+  int split;
+  int ct_cols;   // C^T store groups columns n = q * ct_cols + c into Ct[c][m * (N / ct_cols) + q]
+  int* err;
+};
+cudaError_t tc_gemm_configure();
+cudaError_t launch_sgemm_nt(const TcGemmArgs& g, cudaStream_t st);
+cudaError_t launch_tc_gemm(const TcGemmArgs& g, cudaStream_t st);
+size_t tc_gemm_smem_bytes(int BN, int split, int* stages_out);
+
 cudaError_t launch_site_norm(const double* const* tens, const int64_t* off, const int64_t* len,
                              int nv, int batch, double* inv_norm, double* logscale, int* status,
                              cudaStream_t st);
@@ -53,9 +78,24 @@ cudaError_t launch_close(const double* Y, long long sY, const int64_t* y_off, co
 // eigenvalues, columns signed so the largest-|.| entry is positive) and
 // lam_i[0..nlam) (descending).  One CTA per matrix.
 template <typename T>
-cudaError_t launch_eigh_top(const T* L, long long sL, double* U, long long sU, double* lam,
-                            long long slam, int n, int r, int nlam, int* status, int batch,
+cudaError_t launch_eigh_top(const T* L, long long sL, T* U, long long sU, T* Ut, long long sUt,
+                            double* lam, long long slam, int n, int r, int nlam, int* status,
+                            int batch, cudaStream_t st);
+
+// FP32-storage kernels of the mixed-precision path (see kernels_f32.cu).
+cudaError_t launch_fuse_f32(const FuseSite* sites, int n, int max_elems, const double* const* tens,
+                            const double* inv_norm, int nv, const float* S, long long sS,
+                            int trivial, float* Y, long long sY, float* Yt, const int64_t* yt_off,
+                            int batch, cudaStream_t st);
+cudaError_t launch_fill_env_root_f32(float* R, long long sR, unsigned int* amax, long long s_amax,
+                                     int batch, cudaStream_t st);
+cudaError_t launch_root_f32(const float* P, long long sP, int ldp, const float* Y, long long sY,
+                            int r, int D, int d, float* S_root, float* S_first, int d0,
+                            long long sS, double* logscale, int* status, int batch,
                             cudaStream_t st);
+cudaError_t launch_close_f32(const float* Y, long long sY, const int64_t* y_off, const int32_t* D,
+                             int n, int maxD, const double* logscale, double* logz, int* status,
+                             int batch, cudaStream_t st);
 template <typename T>
 size_t eigh_smem_bytes(int n, int r, int nlam);
 template <typename T>

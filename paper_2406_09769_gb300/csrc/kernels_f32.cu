@@ -1,0 +1,243 @@
+// FP32-storage kernels of the mixed-precision path: block fusion (also writing
+// the transposed block used as a K-major tensor-core operand), the root tensor
+// with its FP64 norm, and the closing contraction.  Sums that feed ln Z are
+// accumulated in FP64.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "kernels.cuh"
+#include "tn_dmtree.h"
+
+namespace tn {
+
+namespace {
+
+__device__ __forceinline__ double block_sum_d(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) red[0] = t;
+  }
+  __syncthreads();
+  return red[0];
+}
+
+__device__ __forceinline__ double block_max_d(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_down_sync(0xffffffffu, t, o));
+    if (threadIdx.x == 0) red[0] = t;
+  }
+  __syncthreads();
+  return red[0];
+}
+
+// Y[a, hl, e, b, hr] = inv_norm * sum_p S[a, p, b] T[p, hl, hr, e]  (FP64 sum, FP32 store)
+// and, when Yt is set, Yt[(e * Dr + b * dhr + hr) * Dl + a * dhl + hl] = same value.
+__global__ void __launch_bounds__(256) k_fuse_f32(const FuseSite* __restrict__ sites,
+                                                  const double* const* tens,
+                                                  const double* __restrict__ inv_norm, int nv,
+                                                  const float* __restrict__ S, long long sS,
+                                                  int trivial, float* __restrict__ Y, long long sY,
+                                                  float* __restrict__ Yt, const int64_t* yt_off) {
+  const FuseSite f = sites[blockIdx.y];
+  const int i = blockIdx.z;
+  const long long total = (long long)f.a * f.dhl * f.de * f.b * f.dhr;
+  const long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= total) return;
+  long long t = o;
+  const int hr = int(t % f.dhr); t /= f.dhr;
+  const int bb = int(t % f.b);   t /= f.b;
+  const int e = int(t % f.de);   t /= f.de;
+  const int hl = int(t % f.dhl); t /= f.dhl;
+  const int aa = int(t);
+  const double* T = tens[i] + f.t_off + hl * f.shl + hr * f.shr + e * f.se;
+  double acc = 0.0;
+  if (trivial) {
+    acc = T[0];
+  } else {
+    const float* Sk = S + (long long)i * sS + f.s_off + (long long)aa * f.dp * f.b + bb;
+    for (int p = 0; p < f.dp; ++p) acc = fma((double)Sk[(long long)p * f.b], T[p * f.sp], acc);
+  }
+  const float v = float(acc * inv_norm[(long long)i * nv + f.vertex]);
+  Y[(long long)i * sY + f.y_off + o] = v;
+  if (Yt) {
+    const long long Dl = (long long)f.a * f.dhl, Dr = (long long)f.b * f.dhr;
+    const long long row = (long long)e * Dr + (long long)bb * f.dhr + hr;
+    Yt[(long long)i * sY + yt_off[blockIdx.y] + row * Dl + (long long)aa * f.dhl + hl] = v;
+  }
+}
+
+__global__ void k_fill_env_root_f32(float* R, long long sR, unsigned int* amax, long long s_amax,
+                                    int batch) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= batch) return;
+  R[(long long)i * sR] = 1.0f;
+  amax[(long long)i * s_amax] = __float_as_uint(1.0f);
+}
+
+// M_r = P (r x D) . Y (D x d), FP64 accumulation and norm; unit-norm FP32
+// store; log-scale += ln ||M_r||; identity boundary site of the first leg.
+__global__ void __launch_bounds__(256) k_root_f32(const float* P, long long sP, int ldp,
+                                                  const float* Y, long long sY, int r, int D,
+                                                  int d, float* S_root, float* S_first, int d0,
+                                                  long long sS, double* logscale, int* status) {
+  __shared__ double red[32];
+  extern __shared__ double mr[];
+  const int i = blockIdx.x;
+  const float* Pi = P + (long long)i * sP;
+  const float* Yi = Y + (long long)i * sY;
+  double ss = 0.0;
+  for (int o = threadIdx.x; o < r * d; o += blockDim.x) {
+    const int a = o / d, e = o % d;
+    double acc = 0.0;
+    for (int k = 0; k < D; ++k)
+      acc = fma((double)Pi[(long long)a * ldp + k], (double)Yi[(long long)k * d + e], acc);
+    mr[o] = acc;
+    ss = fma(acc, acc, ss);
+  }
+  const double nrm = sqrt(block_sum_d(ss, red));
+  const double inv = (nrm > 0.0) ? 1.0 / nrm : 0.0;
+  float* Si = S_root + (long long)i * sS;
+  for (int o = threadIdx.x; o < r * d; o += blockDim.x) Si[o] = float(mr[o] * inv);
+  float* Fi = S_first + (long long)i * sS;
+  for (int o = threadIdx.x; o < d0 * d0; o += blockDim.x) Fi[o] = (o / d0 == o % d0) ? 1.f : 0.f;
+  if (threadIdx.x == 0) {
+    if (!(nrm > 0.0) || !isfinite(nrm)) {
+      if (status[i] == TN_OK) status[i] = TN_ERR_NONFINITE;
+    } else {
+      logscale[i] += log(nrm);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_close_f32(const float* Y, long long sY, const int64_t* y_off,
+                                                   const int32_t* D, int n, const double* logscale,
+                                                   double* logz, int* status) {
+  __shared__ double red[32];
+  extern __shared__ double vbuf[];
+  const int i = blockIdx.x;
+  const float* Yi = Y + (long long)i * sY;
+  int Dl = D[0];
+  double* v = vbuf;
+  double* w = vbuf + D[n];
+  for (int o = threadIdx.x; o < Dl; o += blockDim.x) v[o] = Yi[y_off[0] + o];
+  __syncthreads();
+  double lsum = 0.0;
+  for (int k = 1; k < n; ++k) {
+    const int Dr = D[k];
+    const float* Yk = Yi + y_off[k];
+    double lm = 0.0;
+    for (int c = threadIdx.x; c < Dr; c += blockDim.x) {
+      double acc = 0.0;
+      for (int a = 0; a < Dl; ++a) acc = fma(v[a], (double)Yk[(long long)a * Dr + c], acc);
+      w[c] = acc;
+      lm = fmax(lm, fabs(acc));
+    }
+    const double mx = block_max_d(lm, red);
+    const double inv = (mx > 0.0) ? 1.0 / mx : 1.0;
+    if (mx > 0.0) lsum += log(mx);
+    for (int c = threadIdx.x; c < Dr; c += blockDim.x) v[c] = w[c] * inv;
+    __syncthreads();
+    Dl = Dr;
+  }
+  if (threadIdx.x == 0) {
+    const double s = v[0];
+    int st = status[i];
+    if (st == TN_OK && !isfinite(s)) st = TN_ERR_NONFINITE;
+    if (st == TN_OK && !(s > 0.0)) st = TN_ERR_NONPOSITIVE;
+    status[i] = st;
+    logz[i] = (st == TN_OK) ? log(s) + lsum + logscale[i] : NAN;
+  }
+}
+
+// C_i = alpha_i * A_i B_i^T for shapes the TMA path cannot address (leading
+// dimensions that are not a multiple of 16 bytes); one thread per output,
+// FP64 accumulation.  Same argument semantics as the tensor-core kernel.
+__global__ void __launch_bounds__(256) k_sgemm_nt(TcGemmArgs g) {
+  const int i = blockIdx.z;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = idx < (long long)g.M * g.N;
+  float x = 0.f;
+  if (live) {
+    const int m = int(idx / g.N), n = int(idx % g.N);
+    const float* a = g.A + (long long)i * g.sA + (long long)m * g.lda;
+    const float* b = g.B + (long long)i * g.sB + (long long)n * g.ldb;
+    double acc = 0.0;
+    for (int k = 0; k < g.K; ++k) acc = fma((double)a[k], (double)b[k], acc);
+    float alpha = 1.f;
+    if (g.amax_in) {
+      const float mx = __uint_as_float(g.amax_in[(long long)i * g.s_amax_in]);
+      alpha = (mx > 0.f) ? 1.f / mx : 1.f;
+    }
+    x = float(acc) * alpha;
+    if (g.C) g.C[(long long)i * g.sC + (long long)m * g.ldc + n] = x;
+    if (g.Ct) {
+      const int q = n / g.ct_cols, cc = n - q * g.ct_cols;
+      g.Ct[(long long)i * g.sCt + (long long)cc * g.ldct + (long long)m * (g.N / g.ct_cols) + q] = x;
+    }
+  }
+  if (g.amax_out) {
+    float v = live ? (isfinite(x) ? fabsf(x) : INFINITY) : 0.f;
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(g.amax_out + (long long)i * g.s_amax_out, __float_as_uint(v));
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_sgemm_nt(const TcGemmArgs& g, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
+  if (g.Ct && (g.ct_cols <= 0 || g.N % g.ct_cols)) return cudaErrorInvalidValue;
+  const long long tot = (long long)g.M * g.N;
+  dim3 grid(unsigned((tot + 255) / 256), 1, g.batch);
+  k_sgemm_nt<<<grid, 256, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fuse_f32(const FuseSite* sites, int n, int max_elems, const double* const* tens,
+                            const double* inv_norm, int nv, const float* S, long long sS,
+                            int trivial, float* Y, long long sY, float* Yt, const int64_t* yt_off,
+                            int batch, cudaStream_t st) {
+  dim3 grid((max_elems + 255) / 256, n, batch);
+  k_fuse_f32<<<grid, 256, 0, st>>>(sites, tens, inv_norm, nv, S, sS, trivial, Y, sY, Yt, yt_off);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_env_root_f32(float* R, long long sR, unsigned int* amax, long long s_amax,
+                                     int batch, cudaStream_t st) {
+  k_fill_env_root_f32<<<(batch + 127) / 128, 128, 0, st>>>(R, sR, amax, s_amax, batch);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_root_f32(const float* P, long long sP, int ldp, const float* Y, long long sY,
+                            int r, int D, int d, float* S_root, float* S_first, int d0,
+                            long long sS, double* logscale, int* status, int batch,
+                            cudaStream_t st) {
+  const size_t smem = sizeof(double) * size_t(r) * d;
+  k_root_f32<<<batch, 256, smem, st>>>(P, sP, ldp, Y, sY, r, D, d, S_root, S_first, d0, sS,
+                                       logscale, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_close_f32(const float* Y, long long sY, const int64_t* y_off, const int32_t* D,
+                             int n, int maxD, const double* logscale, double* logz, int* status,
+                             int batch, cudaStream_t st) {
+  const size_t smem = sizeof(double) * size_t(2 * maxD);
+  k_close_f32<<<batch, 256, smem, st>>>(Y, sY, y_off, D, n, logscale, logz, status);
+  return cudaGetLastError();
+}
+
+}  // namespace tn

@@ -1,0 +1,392 @@
+// Batched tensor-core contraction for sm_103a (tcgen05 + TMA + TMEM).
+//
+//   C_i[m][n] = alpha_i * sum_k A_i[m][k] * B_i[n][k]      i = 0 .. batch-1
+//
+// A (M x K) and B (N x K) are row-major FP32 with K contiguous ("K-major"),
+// X_i = X + i * sX.  Every density-matrix contraction of the method is cast in
+// this form (B = R is symmetric; transposed copies are written where needed).
+//
+// One CTA of 128 threads computes a 128 x BN tile (BN <= 256, multiple of 16):
+//   * thread 0 streams 32-wide K chunks of A and B into 128B-swizzled shared
+//     memory with 3D TMA loads (batch = third dimension; out-of-range rows,
+//     columns and K are zero-filled by TMA), through a ring of stages guarded
+//     by mbarriers;
+//   * thread 0 issues tcgen05.mma.cta_group::1.kind::tf32 (M = 128, N = BN,
+//     K = 8 per instruction), accumulating in TMEM (128 lanes x BN columns),
+//     and tcgen05.commit releases each stage;
+//   * with `split`, every staged tile is split in place into x = hi + lo
+//     (hi = x rounded to TF32) and three products hi*hi + hi*lo + lo*hi are
+//     accumulated: the compensated pass of the value path (~FP32 accuracy);
+//   * the four warps read their 32 TMEM lanes with tcgen05.ld.32x32b, scale,
+//     and store C (row-major) and/or C^T, folding max|C| into an atomic slot.
+// Every mbarrier wait is bounded; on expiry the kernel sets *err, waits
+// (bounded) for its own TMA copies, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+
+#include "kernels.cuh"
+
+namespace tn {
+
+namespace {
+
+constexpr int kTcThreads = 128;
+constexpr int kChunk = 32;                    // K elements per stage (128 bytes of FP32)
+constexpr uint32_t kWaitLimit = 1u << 22;     // bounded spin on every mbarrier
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+  for (uint32_t i = 0; i < kWaitLimit; ++i)
+    if (mbar_try(b, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
+                                            int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(su32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(su32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128B swizzle, rows of 128 B,
+// 8-row groups 1024 B apart (stride byte offset), fixed version bits 46..48 = 1.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= uint64_t((saddr >> 4) & 0x3FFFu);
+  d |= uint64_t(1) << 16;                 // leading byte offset (unused for swizzled K-major)
+  d |= uint64_t(1024 >> 4) << 32;         // stride byte offset
+  d |= uint64_t(1) << 46;                 // descriptor version
+  d |= uint64_t(2) << 61;                 // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor, kind::tf32: D = F32, A = B = TF32, both K-major.
+__host__ __device__ __forceinline__ uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ float tf32_hi(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+struct SmemPlan {
+  uint32_t a_bytes, b_bytes, stage_bytes, stages, split;
+};
+
+__global__ void __launch_bounds__(kTcThreads) k_tc_gemm(const __grid_constant__ CUtensorMap tmA,
+                                                      const __grid_constant__ CUtensorMap tmB,
+                                                      TcGemmArgs g, int BN, int stages,
+                                                      uint32_t tmem_cols) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte alignment of the stage ring (required by the 128B swizzle atoms)
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t a_bytes = 128 * 128;
+  const uint32_t b_bytes = uint32_t(BN) * 128;
+  const uint32_t tile_bytes = a_bytes + b_bytes;
+  const uint32_t stage_bytes = g.split ? 2 * tile_bytes : tile_bytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + stages * stage_bytes);
+  uint64_t* freed = full + stages;
+  uint64_t* done = freed + stages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * 128, bi = blockIdx.z;
+  const int nk = (g.K + kChunk - 1) / kChunk;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(tmem_slot)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&freed[s], 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t idesc = idesc_tf32(128, BN);
+
+  int issued = 0;    // chunks whose TMA has been issued (thread 0)
+  int consumed = 0;  // chunks whose arrival thread 0 has observed
+  auto issue = [&](int kc) {
+    const int s = kc % stages;
+    unsigned char* st = base + s * stage_bytes;
+    mbar_expect_tx(&full[s], tile_bytes);
+    tma_load_3d(st, &tmA, &full[s], kc * kChunk, m0, bi);
+    tma_load_3d(st + a_bytes, &tmB, &full[s], kc * kChunk, n0, bi);
+  };
+  if (tid == 0) {
+    for (; issued < nk && issued < stages; ++issued) issue(issued);
+  }
+  bool ok = true;
+  for (int kc = 0; kc < nk; ++kc) {
+    const int s = kc % stages;
+    const uint32_t ph = uint32_t(kc / stages) & 1u;
+    unsigned char* st = base + s * stage_bytes;
+    if (g.split) {
+      // every thread waits for the chunk, then splits it in place (hi) and
+      // into the lo copy; the async proxy sees the writes after the fence.
+      const bool arrived = mbar_wait(&full[s], ph);
+      if (!arrived) atomicExch(abort_flag, 1);
+      if (tid == 0 && arrived) consumed = kc + 1;
+      __syncthreads();
+      if (*abort_flag) { ok = false; break; }
+      float4* hi = reinterpret_cast<float4*>(st);
+      float4* lo = reinterpret_cast<float4*>(st + tile_bytes);
+      for (uint32_t q = tid; q < tile_bytes / 16; q += kTcThreads) {
+        float4 x = hi[q];
+        float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+        hi[q] = h;
+        lo[q] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+    }
+    if (tid == 0) {
+      if (!g.split) {
+        if (mbar_wait(&full[s], ph)) {
+          consumed = kc + 1;
+        } else {
+          *abort_flag = 1;
+          ok = false;
+        }
+      }
+      if (ok) {
+        tc_fence_after();
+        const uint32_t a0 = su32(st), b0 = su32(st + a_bytes);
+        for (int j = 0; j < kChunk / 8; ++j) {
+          const uint32_t acc = (kc > 0 || j > 0) ? 1u : 0u;
+          const uint64_t ah = desc_sw128(a0 + 32 * j), bh = desc_sw128(b0 + 32 * j);
+          umma_tf32(tmem, ah, bh, idesc, acc);
+          if (g.split) {
+            const uint64_t al = desc_sw128(a0 + tile_bytes + 32 * j);
+            const uint64_t bl = desc_sw128(b0 + tile_bytes + 32 * j);
+            umma_tf32(tmem, ah, bl, idesc, 1u);
+            umma_tf32(tmem, al, bh, idesc, 1u);
+          }
+        }
+        umma_commit(&freed[s]);
+        if (issued < nk) {
+          // the stage is reloaded once the MMAs reading it have completed
+          if (!mbar_wait(&freed[s], ph)) {
+            *abort_flag = 1;
+            ok = false;
+          } else {
+            issue(issued);
+            ++issued;
+          }
+        }
+      }
+    }
+    if (!ok) break;
+  }
+  if (tid == 0 && ok) umma_commit(done);
+  __syncthreads();
+  bool good = (*abort_flag == 0);
+  if (good && !mbar_wait(done, 0)) good = false;
+  if (!__syncthreads_and(good)) {
+    good = false;
+    if (tid == 0) {
+      atomicExch(g.err, 1);
+      // drain: TMA chunks still in flight must land before the CTA exits
+      for (int kc = consumed; kc < issued; ++kc)
+        mbar_wait(&full[kc % stages], uint32_t(kc / stages) & 1u);
+    }
+  }
+  __syncthreads();
+  tc_fence_after();
+  if (good) {
+    float alpha = 1.f;
+    if (g.amax_in) {
+      const float mx = __uint_as_float(g.amax_in[(long long)bi * g.s_amax_in]);
+      alpha = (mx > 0.f) ? 1.f / mx : 1.f;
+    }
+    const int row = warp * 32 + lane;
+    const int gm = m0 + row;
+    float lmax = 0.f;
+    bool bad = false;
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      uint32_t v[16];
+      tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(c0), v);
+      if (gm < g.M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int gn = n0 + c0 + j;
+          if (gn >= g.N) break;
+          const float x = alpha * __uint_as_float(v[j]);
+          if (g.C) g.C[(long long)bi * g.sC + (long long)gm * g.ldc + gn] = x;
+          if (g.Ct) {
+            const int q = gn / g.ct_cols, cc = gn - q * g.ct_cols;
+            g.Ct[(long long)bi * g.sCt + (long long)cc * g.ldct + (long long)gm * (g.N / g.ct_cols) + q] = x;
+          }
+          lmax = fmaxf(lmax, fabsf(x));
+          bad |= !isfinite(x);
+        }
+      }
+    }
+    if (g.amax_out) {
+      if (bad) lmax = INFINITY;
+      for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+      if (lane == 0) atomicMax(g.amax_out + (long long)bi * g.s_amax_out, __float_as_uint(lmax));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, const float* ptr, int K, int rows, int batch, long long ld,
+              long long sBatch, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {cuuint64_t(K), cuuint64_t(rows), cuuint64_t(batch)};
+  cuuint64_t strides[2] = {cuuint64_t(ld) * 4, cuuint64_t(sBatch) * 4};
+  cuuint32_t box[3] = {uint32_t(kChunk), uint32_t(box_rows), 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(ptr), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+size_t tc_gemm_smem_bytes(int BN, int split, int* stages_out) {
+  const size_t tile = size_t(128 + BN) * 128;
+  const size_t stage = split ? 2 * tile : tile;
+  int stages = int((200 * 1024) / stage);
+  if (stages > 4) stages = 4;
+  if (stages < 1) stages = 1;
+  if (stages_out) *stages_out = stages;
+  return 1024 + stages * stage + (2 * stages + 1) * 8 + 16;
+}
+
+cudaError_t tc_gemm_configure() {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  if (!encode_fn()) return cudaErrorNotSupported;
+  return cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+}
+
+cudaError_t launch_tc_gemm(const TcGemmArgs& g, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
+  if (g.Ct && (g.ct_cols <= 0 || g.N % g.ct_cols)) return cudaErrorInvalidValue;
+  if (g.K <= 0 || (g.lda % 4) || (g.ldb % 4) || (g.sA % 4) || (g.sB % 4) ||
+      (reinterpret_cast<uintptr_t>(g.A) % 16) || (reinterpret_cast<uintptr_t>(g.B) % 16))
+    return cudaErrorInvalidValue;
+  int BN = ((g.N + 15) / 16) * 16;
+  if (BN > 256) BN = 256;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, g.A, g.K, g.M, g.batch, g.lda, g.sA, 128)) return cudaErrorInvalidValue;
+  if (!make_map(&mb, g.B, g.K, g.N, g.batch, g.ldb, g.sB, BN)) return cudaErrorInvalidValue;
+  int stages = 1;
+  const size_t smem = tc_gemm_smem_bytes(BN, g.split, &stages);
+  uint32_t cols = 32;
+  while (cols < uint32_t(BN)) cols <<= 1;
+  dim3 grid((g.N + BN - 1) / BN, (g.M + 127) / 128, g.batch);
+  k_tc_gemm<<<grid, kTcThreads, smem, st>>>(ma, mb, g, BN, stages, cols);
+  return cudaGetLastError();
+}
+
+}  // namespace tn

@@ -1,0 +1,87 @@
+"""GPU parity of the mixed-precision (TF32 tensor-core) path against the FP64
+oracle.  Bar: relative ln Z error <= 1e-6 with the same chi (the truncation is
+the oracle's, so this is the error the mixed precision adds beyond it)."""
+import numpy as np
+import pytest
+
+from oracle import dmtree
+from paper_2406_09769_gb300 import binding as B
+from workloads import ising
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+RTOL_MIXED = 1e-6
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import os
+    if not os.path.exists(B.LIB_PATH):
+        from paper_2406_09769_gb300 import build
+        build.build()
+    return B.tn_ctx_create(0)
+
+
+def _run(ctx, ws, chi, precision):
+    plans = [B.tn_plan(w["n"], w["edges"], np.full(len(w["edges"]), 2), chi, env_size=w["Ly"])
+             for w in ws]
+    bufs = [torch.from_numpy(B.pack_sites(p, w["tensors"])).cuda() for p, w in zip(plans, ws)]
+    B.tn_contract_approx(ctx, plans, [b.data_ptr() for b in bufs], precision, 0,
+                         torch.cuda.current_stream().cuda_stream)
+    return B.tn_logz(ctx, len(plans))
+
+
+def test_tf32_config1_exact(ctx):
+    w = ising.lattice2d(6, 6, 0.44)
+    logz, status = _run(ctx, [w], 16, B.TN_PREC_TF32)
+    assert status[0] == 0
+    assert abs(logz[0] - 31.564145959482058) <= RTOL_MIXED * 31.6
+
+
+@pytest.mark.parametrize("Lx,Ly,beta,cp,chi", [
+    (6, 9, 0.8, "gauss", 4), (8, 8, 0.5, "gauss", 6), (7, 10, 1.0, "pm1", 5),
+    (3, 11, 0.6, "gauss", 3), (2, 7, 0.5, "gauss", 4), (7, 3, 0.9, "gauss", 1),
+    (12, 14, 0.7, "gauss", 17), (16, 16, 0.5, "gauss", 32)])
+def test_tf32_matches_oracle(ctx, Lx, Ly, beta, cp, chi):
+    ws = [ising.lattice2d(Lx, Ly, beta, cp, seed=500 * Lx + Ly + i) for i in range(4)]
+    logz, status = _run(ctx, ws, chi, B.TN_PREC_TF32)
+    assert list(status) == [0] * 4
+    for i, w in enumerate(ws):
+        ref = dmtree.partitioned_contract_rows(w, chi)["logz"]
+        assert abs(logz[i] - ref) <= RTOL_MIXED * abs(ref), (i, logz[i], ref)
+
+
+@pytest.mark.parametrize("chi", [32, 64])
+def test_tf32_full_size_config2_sampled(ctx, chi):
+    n_inst = 8
+    ws = [ising.config2_instance(i) for i in range(n_inst)]
+    logz, status = _run(ctx, ws, chi, B.TN_PREC_TF32)
+    fp64, st64 = _run(ctx, ws, chi, B.TN_PREC_FP64)
+    assert list(status) == [0] * n_inst and list(st64) == [0] * n_inst
+    assert np.max(np.abs(logz - fp64) / np.abs(fp64)) <= RTOL_MIXED
+    for i in (0, n_inst - 1):
+        ref = dmtree.partitioned_contract_rows(ws[i], chi)["logz"]
+        assert abs(logz[i] - ref) <= RTOL_MIXED * abs(ref), (i, logz[i], ref)
+
+
+def test_tf32_nonfinite_instance_is_isolated(ctx):
+    ws = [ising.lattice2d(6, 8, 0.6, "gauss", seed=s) for s in range(3)]
+    bad = dict(ws[2])
+    bad["tensors"] = [t.copy() for t in ws[2]["tensors"]]
+    bad["tensors"][5].flat[3] = np.inf
+    logz, status = _run(ctx, [ws[0], ws[1], bad], 4, B.TN_PREC_TF32)
+    assert list(status) == [0, 0, 4]
+    for i in (0, 1):
+        ref = dmtree.partitioned_contract_rows(ws[i], 4)["logz"]
+        assert abs(logz[i] - ref) <= RTOL_MIXED * abs(ref)
+
+
+def test_unsupported_precision_is_reported(ctx):
+    w = ising.lattice2d(4, 4, 0.5)
+    with pytest.raises(B.TNError) as e:
+        _run(ctx, [w], 4, B.TN_PREC_BF16)
+    assert e.value.status == 8
