@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "bf16"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "tf32fast", "bf16"])
     p.add_argument("--chi", type=int, default=64)
     p.add_argument("--size", type=int, default=32)
     p.add_argument("--batch", type=int, default=304)
@@ -226,7 +226,8 @@ def bench_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    prec = {"fp64": B.TN_PREC_FP64, "tf32": B.TN_PREC_TF32, "bf16": B.TN_PREC_BF16}[args.precision]
+    prec = {"fp64": B.TN_PREC_FP64, "tf32": B.TN_PREC_TF32, "tf32fast": B.TN_PREC_TF32_FAST,
+            "bf16": B.TN_PREC_BF16}[args.precision]
     Bn, K, W = args.batch, args.steps, args.warmup
 
     # workload (rank r owns instances r*B .. r*B+B-1)
@@ -326,8 +327,9 @@ def bench_ours(args):
         bound, peak, note = "alu", FP32_ALU_TFLOPS, "FP32 152 SMs x 128 lanes x 2 x 2.07 GHz"
     else:
         bf16 = pk.get("bf16_tflops_sustained", FALLBACK["bf16_tflops_sustained"])
-        peak = bf16 * (TF32_PER_BF16 if prec == B.TN_PREC_TF32 else 1.0)
-        bound, note = "tensor", f"{pk_src} bf16 sustained" + (" x 1.1/2.25 (tf32)" if prec == B.TN_PREC_TF32 else "")
+        is_tf32 = prec in (B.TN_PREC_TF32, B.TN_PREC_TF32_FAST)
+        peak = bf16 * (TF32_PER_BF16 if is_tf32 else 1.0)
+        bound, note = "tensor", f"{pk_src} bf16 sustained" + (" x 1.1/2.25 (tf32)" if is_tf32 else "")
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
@@ -345,7 +347,7 @@ def bench_ours(args):
         "metric": "approx contractions/s", "value": value, "unit": "contractions/s",
         "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": total_ms / K,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "f64", "tf32": "tf32", "bf16": "bf16"}[args.precision],
+        "dtype": {"fp64": "f64", "tf32": "tf32", "tf32fast": "tf32", "bf16": "bf16"}[args.precision],
         "data": "synthetic (seeded instances)",
         "config": {"workload": WORKLOAD, "size": args.size, "chi": args.chi, "batch": Bn,
                    "precision": args.precision, "l2": "flushed between steps (256 MB write)",

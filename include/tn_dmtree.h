@@ -46,15 +46,18 @@ typedef enum {
 } tn_status;
 
 /* Arithmetic of the hot path.
- *   TN_PREC_FP64: every contraction, eigensolver and scale in FP64.
- *   TN_PREC_TF32: density-matrix contractions on tcgen05 tensor cores with
- *                 TF32 inputs and FP32 accumulation; the value path (local
- *                 block, projector, root) with a 3-term TF32 split
- *                 (compensated); eigensolver reduction in FP32 with FP64
- *                 eigenvalue refinement; log-scale in FP64.
- *   TN_PREC_BF16: as TF32 but BF16 operands (3-term BF16 split on the value
- *                 path).                                                     */
-enum { TN_PREC_FP64 = 0, TN_PREC_BF16 = 1, TN_PREC_TF32 = 2 };
+ *   TN_PREC_FP64:      every contraction, eigensolver and scale in FP64.
+ *   TN_PREC_TF32:      FP32 storage; every contraction on tcgen05 tensor cores
+ *                      as a compensated 3-term TF32 split (hi*hi + hi*lo +
+ *                      lo*hi, FP32 accumulation, ~FP32 accuracy); FP32
+ *                      eigensolver; root norm, log-scale and the closing
+ *                      contraction in FP64.
+ *   TN_PREC_TF32_FAST: as TN_PREC_TF32 but the density-matrix side (memoised
+ *                      environments, L_v) in plain TF32; only the value path
+ *                      (local blocks, projections) is compensated.  Loses
+ *                      eigen-directions below ~1e-3 of the largest eigenvalue.
+ *   TN_PREC_BF16:      reserved; returns TN_ERR_UNSUPPORTED in this build.  */
+enum { TN_PREC_FP64 = 0, TN_PREC_BF16 = 1, TN_PREC_TF32 = 2, TN_PREC_TF32_FAST = 3 };
 
 /* The tensor network graph G = (V, E) of Sec. 2.1.  Host memory, caller-owned.
  * edge_v[e] == -1 marks an open (uncontracted) edge; this build requires a

@@ -18,7 +18,7 @@ TN_OK = 0
 STATUS_NAMES = {0: "TN_OK", 1: "TN_ERR_INVALID", 2: "TN_ERR_OOM", 3: "TN_ERR_CUDA",
                 4: "TN_ERR_NONFINITE", 5: "TN_ERR_NONPOSITIVE", 6: "TN_ERR_TIMEOUT",
                 7: "TN_ERR_EIG_NOCONV", 8: "TN_ERR_UNSUPPORTED"}
-TN_PREC_FP64, TN_PREC_BF16, TN_PREC_TF32 = 0, 1, 2
+TN_PREC_FP64, TN_PREC_BF16, TN_PREC_TF32, TN_PREC_TF32_FAST = 0, 1, 2, 3
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _vp = ctypes.c_void_p

@@ -528,8 +528,9 @@ void tgemm(tn_ctx* c, int cls, const float* A, long long sA, int lda, const floa
   }
 }
 
+// sub_split: compensated products also on the density-matrix side (env, L_v).
 void dm_pass_tc(tn_ctx* c, const tn::Step& st, const Lay& l, const WsF& w, float* Snext, int B,
-                cudaStream_t strm) {
+                int sub_split, cudaStream_t strm) {
   const int n = st.n;
   const auto& D = st.D;
   const auto& d = st.d;
@@ -537,15 +538,16 @@ void dm_pass_tc(tn_ctx* c, const tn::Step& st, const Lay& l, const WsF& w, float
   Scope(c, TN_KC_ENV, strm),
   ck(tn::launch_fill_env_root_f32(w.R + l.r_off[n - 1], w.sR, w.amax + (n - 1), w.sAmax, B, strm),
      "env root");
-  // Memoised root-side density matrices, Eq. (dm_cache) (subspace path, TF32).
+  // Memoised root-side density matrices, Eq. (dm_cache).
   // B = R_k enters as its own transpose: R_k is symmetric.
   for (int k = n - 1; k >= 2; --k) {
     const float* Yk = w.Y + l.y_off[k];
     const int Dl = D[k - 1], Dr = D[k], dk = d[k];
     tgemm(c, TN_KC_ENV, Yk, w.sY, Dr, w.R + l.r_off[k], w.sR, Dr, w.X, w.sX, Dr, nullptr, 0, 0, 0,
-          Dl * dk, Dr, Dr, B, w.amax + k, w.sAmax, nullptr, 0, 0, strm);
+          Dl * dk, Dr, Dr, B, w.amax + k, w.sAmax, nullptr, 0, sub_split, strm);
     tgemm(c, TN_KC_ENV, w.X, w.sX, dk * Dr, Yk, w.sY, dk * Dr, w.R + l.r_off[k - 1], w.sR, Dl,
-          nullptr, 0, 0, 0, Dl, Dl, dk * Dr, B, nullptr, 0, w.amax + (k - 1), w.sAmax, 0, strm);
+          nullptr, 0, 0, 0, Dl, Dl, dk * Dr, B, nullptr, 0, w.amax + (k - 1), w.sAmax, sub_split,
+          strm);
   }
   for (int k = 1; k <= n - 2; ++k) {
     const int rp = st.r[k - 1], rk = st.r[k], dk = d[k], Dl = D[k - 1], Dr = D[k];
@@ -555,11 +557,11 @@ void dm_pass_tc(tn_ctx* c, const tn::Step& st, const Lay& l, const WsF& w, float
     // M_v = P_{v-1} Y_v (value path, compensated); also M_v^T for the projector.
     tgemm(c, TN_KC_LOCAL, Pp, sPp, Dl, w.Yt + l.y_off[k], w.sY, Dl, w.M, w.sM, dk * Dr, w.Mt,
           w.sM, A, Dr, rp, dk * Dr, Dl, B, nullptr, 0, nullptr, 0, 1, strm);
-    // L_v = M_v R_k M_v^T (subspace path)
+    // L_v = M_v R_k M_v^T
     tgemm(c, TN_KC_DENSITY, w.M, w.sM, Dr, w.R + l.r_off[k], w.sR, Dr, w.G, w.sM, Dr, nullptr, 0, 0,
-          0, A, Dr, Dr, B, w.amax + k, w.sAmax, nullptr, 0, 0, strm);
+          0, A, Dr, Dr, B, w.amax + k, w.sAmax, nullptr, 0, sub_split, strm);
     tgemm(c, TN_KC_DENSITY, w.G, w.sM, Dr, w.M, w.sM, Dr, w.L, w.sL, A, nullptr, 0, 0, 0, A, A, Dr,
-          B, nullptr, 0, nullptr, 0, 0, strm);
+          B, nullptr, 0, nullptr, 0, sub_split, strm);
     float* Uk = Snext + l.s_off[k];
     Scope(c, TN_KC_EIG, strm),
     ck(tn::launch_eigh_top<float>(w.L, w.sL, Uk, w.sS, w.Ut, w.sUt, w.lam, w.sLam, A, rk, 0,
@@ -577,7 +579,7 @@ void dm_pass_tc(tn_ctx* c, const tn::Step& st, const Lay& l, const WsF& w, float
 }
 
 void run_plan_tc(tn_ctx* c, const tn_plan_t* P, int B, const double* const* tens_dev,
-                 cudaStream_t strm) {
+                 int sub_split, cudaStream_t strm) {
   std::vector<Lay> lay;
   for (const tn::Step& st : P->steps) lay.push_back(lay_f32(st));
   ensure_results(c, B);
@@ -611,7 +613,7 @@ void run_plan_tc(tn_ctx* c, const tn_plan_t* P, int B, const double* const* tens
       ck(tn::launch_fuse_f32(tabs[s].fuse, st.n, maxe, tens_table, w.inv, P->n_vertices, Scur,
                              w.sS, 0, w.Y, w.sY, w.Yt, tabs[s].y_off, B, strm),
          "fuse");
-      dm_pass_tc(c, st, lay[s], w, Snext, B, strm);
+      dm_pass_tc(c, st, lay[s], w, Snext, B, sub_split, strm);
       std::swap(Scur, Snext);
     } else {
       Scope(c, TN_KC_FUSE, strm),
@@ -722,9 +724,9 @@ extern "C" tn_status tn_contract_approx(tn_ctx_t* c, const tn_plan_t* const* pla
     cudaStream_t strm = static_cast<cudaStream_t>(stream);
     if (precision == TN_PREC_FP64) {
       run_plan(c, plans[0], n_inst, sites_dev, precision, strm);
-    } else if (precision == TN_PREC_TF32) {
+    } else if (precision == TN_PREC_TF32 || precision == TN_PREC_TF32_FAST) {
       if (!c->tc_ready) fail(TN_ERR_UNSUPPORTED, "tcgen05 path unavailable on this device");
-      run_plan_tc(c, plans[0], n_inst, sites_dev, strm);
+      run_plan_tc(c, plans[0], n_inst, sites_dev, precision == TN_PREC_TF32 ? 1 : 0, strm);
     } else {
       fail(TN_ERR_UNSUPPORTED, "precision mode not implemented in this build");
     }

@@ -80,6 +80,17 @@ def test_tf32_nonfinite_instance_is_isolated(ctx):
         assert abs(logz[i] - ref) <= RTOL_MIXED * abs(ref)
 
 
+def test_tf32_fast_mode_error_is_bounded(ctx):
+    """Plain TF32 on the density-matrix side: directions below ~1e-3 of the
+    top eigenvalue are resolved only to TF32 noise; the measured cost on the
+    32x32 chi=64 workload is a few 1e-6 relative in ln Z (bound 2e-5 here)."""
+    ws = [ising.config2_instance(i) for i in range(4)]
+    fast, st = _run(ctx, ws, 64, B.TN_PREC_TF32_FAST)
+    fp64, st64 = _run(ctx, ws, 64, B.TN_PREC_FP64)
+    assert list(st) == [0] * 4 and list(st64) == [0] * 4
+    assert np.max(np.abs(fast - fp64) / np.abs(fp64)) <= 2e-5
+
+
 def test_unsupported_precision_is_reported(ctx):
     w = ising.lattice2d(4, 4, 0.5)
     with pytest.raises(B.TNError) as e:
