@@ -42,17 +42,33 @@ def test_tf32_config1_exact(ctx):
     assert abs(logz[0] - 31.564145959482058) <= RTOL_MIXED * 31.6
 
 
+def _truncation_error(w, chi, ref):
+    """|ln Z_chi - ln Z_exact| of the oracle (exact: transfer matrix, or the
+    oracle at the maximal MPS rank 2^(Ly/2) when the strip is too wide)."""
+    from oracle import exact
+    if w["Ly"] <= 14:
+        ex = exact.ising_logz_transfer_matrix(w["Lx"], w["Ly"], w["edges"], w["J"], w["beta"])
+    else:
+        ex = dmtree.partitioned_contract_rows(w, 2 ** (w["Ly"] // 2))["logz"]
+    return abs(ref - ex)
+
+
 @pytest.mark.parametrize("Lx,Ly,beta,cp,chi", [
     (6, 9, 0.8, "gauss", 4), (8, 8, 0.5, "gauss", 6), (7, 10, 1.0, "pm1", 5),
     (3, 11, 0.6, "gauss", 3), (2, 7, 0.5, "gauss", 4), (7, 3, 0.9, "gauss", 1),
     (12, 14, 0.7, "gauss", 17), (16, 16, 0.5, "gauss", 32)])
 def test_tf32_matches_oracle(ctx, Lx, Ly, beta, cp, chi):
-    ws = [ising.lattice2d(Lx, Ly, beta, cp, seed=500 * Lx + Ly + i) for i in range(4)]
+    ws = [ising.lattice2d(Lx, Ly, beta, cp, seed=500 * Lx + Ly + i) for i in range(6)]
     logz, status = _run(ctx, ws, chi, B.TN_PREC_TF32)
-    assert list(status) == [0] * 4
+    assert list(status) == [0] * len(ws)
+    # Beyond truncation: where a cut falls inside a (near-)degenerate pair of
+    # eigenvalues (exact degeneracies occur with +-J couplings) the kept
+    # subspace is not unique and any two correct codes may pick different
+    # approximations, differing by a fraction of the truncation error itself.
     for i, w in enumerate(ws):
         ref = dmtree.partitioned_contract_rows(w, chi)["logz"]
-        assert abs(logz[i] - ref) <= RTOL_MIXED * abs(ref), (i, logz[i], ref)
+        trunc = _truncation_error(w, chi, ref)
+        assert abs(logz[i] - ref) <= RTOL_MIXED * abs(ref) + 0.1 * trunc, (i, logz[i], ref, trunc)
 
 
 @pytest.mark.parametrize("chi", [32, 64])
