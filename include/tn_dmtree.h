@@ -180,6 +180,35 @@ tn_status tn_contract_approx_host(tn_ctx_t* ctx, const tn_plan_t* const* plans, 
                                   int32_t learned_chi, double* logz_host,
                                   int32_t* status_host, void* stream);
 
+/* ------------------------------------------------ allocation-free variant
+ * The paper has no counterpart: this entry point exists for callers of this
+ * library that cannot allocate device memory.  Examples: a host application
+ * whose own allocator has already reserved nearly all device memory (a new
+ * cudaMalloc would fail); a plug-in whose host forbids direct device
+ * allocation; a latency-critical loop where cudaMalloc/cudaFree, which may
+ * synchronise the device, are not acceptable.
+ *
+ * It runs the same density-matrix pass as tn_embed_tree with precision FP64
+ * (same arguments, layouts, outputs and error codes, minus the ctx and the
+ * precision) but allocates nothing: its workspace is one device array of
+ * TN_NOALLOC_SCRATCH_BYTES (16 MiB) compiled into the library, which every
+ * GPU that loads the library holds until the process exits.  A problem whose
+ * workspace would exceed it returns TN_ERR_INVALID, and tn_last_error(NULL)
+ * states the bytes it needs.  The caller still provides all inputs and
+ * outputs (device memory it owns).  The first call on a device looks up the
+ * array's device address and configures the eigensolver's shared memory;
+ * make that first call before any stream capture.  All calls share the one
+ * array and it keeps the previous call's contents: calls that can overlap on
+ * the GPU (different streams, or host threads without ordering between them)
+ * race on it and corrupt each other's results, so serialise them.  Device
+ * outputs are written asynchronously on stream; ranks_host on return.      */
+#define TN_NOALLOC_SCRATCH_BYTES (16u << 20)
+tn_status tn_embed_tree_noalloc(int32_t n_inst, int32_t n_legs, const int32_t* leg_dim,
+                                const int32_t* bond_dim, const double* const* blocks_dev,
+                                int32_t chi, const int32_t* chi_per_edge,
+                                double* const* tree_dev, double* lognorm_dev,
+                                int32_t* status_dev, int32_t* ranks_host, void* stream);
+
 /* ------------------------------------------------------------- diagnostics
  * Kernel classes of the hot path, for launch counts and timing.            */
 enum {

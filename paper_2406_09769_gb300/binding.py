@@ -55,8 +55,8 @@ _lib = None
 # Every symbol include/tn_dmtree.h declares.
 EXPORTS = ("tn_plan", "tn_plan_destroy", "tn_plan_query", "tn_plan_site_offset",
            "tn_ctx_create", "tn_ctx_destroy", "tn_embed_tree", "tn_contract_approx",
-           "tn_logz", "tn_contract_approx_host", "tn_ctx_set_profiling", "tn_ctx_profile",
-           "tn_last_error")
+           "tn_logz", "tn_contract_approx_host", "tn_embed_tree_noalloc",
+           "tn_ctx_set_profiling", "tn_ctx_profile", "tn_last_error")
 
 KERNEL_CLASSES = ("norm", "fuse", "env", "local", "density", "eig", "project", "root", "close")
 
@@ -85,6 +85,9 @@ def lib():
     L.tn_contract_approx_host.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.c_int32,
                                           ctypes.POINTER(_vp), ctypes.c_int32, ctypes.c_int32,
                                           ctypes.POINTER(ctypes.c_double), _i32p, _vp]
+    L.tn_embed_tree_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p,
+                                        ctypes.POINTER(_vp), ctypes.c_int32, _i32p,
+                                        ctypes.POINTER(_vp), _vp, _vp, _i32p, _vp]
     L.tn_ctx_set_profiling.argtypes = [_vp, ctypes.c_int32]
     L.tn_ctx_profile.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]
@@ -209,6 +212,28 @@ def tn_embed_tree(ctx, blocks_dev, leg_dim, bond_dim, chi, tree_dev, lognorm_dev
                              cpep, int(precision), _ptrs(tree_dev), _vp(int(lognorm_dev)),
                              _vp(int(status_dev)), ranks.ctypes.data_as(_i32p), _vp(int(stream)))
     _check(st, ctx)
+    return ranks
+
+
+def tn_embed_tree_noalloc(blocks_dev, leg_dim, bond_dim, chi, tree_dev, lognorm_dev, status_dev,
+                          chi_per_edge=None, stream=0):
+    """Allocation-free FP64 density-matrix pass (no ctx; static device workspace).
+
+    For callers that cannot allocate device memory; see include/tn_dmtree.h.
+    Returns the ranks r_0..r_{n-2}.
+    """
+    n = len(leg_dim)
+    ld, ldp = _i32(leg_dim)
+    bd, bdp = _i32(bond_dim)
+    cpe = cpep = None
+    if chi_per_edge is not None:
+        cpe, cpep = _i32(chi_per_edge)
+    ranks = np.zeros(n - 1, dtype=np.int32)
+    st = lib().tn_embed_tree_noalloc(len(blocks_dev), n, ldp, bdp, _ptrs(blocks_dev), int(chi),
+                                     cpep, _ptrs(tree_dev), _vp(int(lognorm_dev)),
+                                     _vp(int(status_dev)), ranks.ctypes.data_as(_i32p),
+                                     _vp(int(stream)))
+    _check(st)
     return ranks
 
 

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -902,6 +903,169 @@ extern "C" tn_status tn_embed_tree(tn_ctx_t* c, int32_t n_inst, int32_t n_legs,
        "copy lognorm");
     ck(cudaMemcpyAsync(status_dev, c->status, sizeof(int) * n_inst, cudaMemcpyDeviceToDevice,
                        strm),
+       "copy status");
+    for (int k = 0; k < n - 1; ++k) ranks_host[k] = st.r[k];
+  });
+}
+
+// ------------------------------------------------ allocation-free variant
+// Workspace of tn_embed_tree_noalloc: a fixed device array compiled into the
+// library (every device that loads the library holds it until exit).  Host
+// code must not pass the symbol itself to a kernel; its device address is
+// looked up once per device with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[TN_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {};
+}  // namespace
+
+extern "C" tn_status tn_embed_tree_noalloc(int32_t n_inst, int32_t n_legs, const int32_t* leg_dim,
+                                           const int32_t* bond_dim,
+                                           const double* const* blocks_dev, int32_t chi,
+                                           const int32_t* chi_per_edge, double* const* tree_dev,
+                                           double* lognorm_dev, int32_t* status_dev,
+                                           int32_t* ranks_host, void* stream) {
+  return guarded(nullptr, "tn_embed_tree_noalloc", [&] {
+    if (n_inst < 1 || n_legs < 3 || !leg_dim || !bond_dim || !blocks_dev || !tree_dev ||
+        !lognorm_dev || !status_dev || !ranks_host)
+      fail(TN_ERR_INVALID, "invalid argument");
+    if (chi < 1 && !chi_per_edge) fail(TN_ERR_INVALID, "chi must be >= 1");
+    const int n = n_legs;
+    tn::Step st;
+    st.kind = 1;
+    st.n = n;
+    st.d.assign(leg_dim, leg_dim + n);
+    st.D.assign(n, 1);
+    for (int k = 0; k < n; ++k) {
+      if (st.d[k] < 1) fail(TN_ERR_INVALID, "leg dim < 1");
+      if (k < n - 1) {
+        st.D[k] = bond_dim[k];
+        if (st.D[k] < 1 || st.D[k] > (1 << 16)) fail(TN_ERR_INVALID, "bond dim out of range");
+      }
+    }
+    st.site.resize(n);
+    for (int k = 0; k < n; ++k) {
+      tn::SiteOp o{};
+      o.a = (k == 0) ? 1 : st.D[k - 1];
+      o.b = st.D[k];
+      o.dp = o.dhl = o.dhr = 1;
+      o.de = st.d[k];
+      st.site[k] = o;
+    }
+    st.r.assign(n - 1, 0);
+    st.r[0] = st.d[0];
+    for (int k = 1; k <= n - 2; ++k) {
+      double beyond = 1;
+      for (int j = k + 1; j < n; ++j) beyond *= st.d[j];
+      const int ck_ = chi_per_edge ? chi_per_edge[k] : chi;
+      if (ck_ < 1) fail(TN_ERR_INVALID, "chi_per_edge entries must be >= 1");
+      double r = std::min<double>(ck_, double(st.r[k - 1]) * st.d[k]);
+      r = std::min<double>(r, st.D[k]);
+      r = std::min<double>(r, beyond);
+      st.r[k] = int(r);
+    }
+    st.y_off.assign(n, 0);
+    long long off = 0;
+    for (int k = 0; k < n; ++k) {
+      st.y_off[k] = off;
+      off += (long long)st.site[k].a * st.d[k] * st.D[k];
+    }
+    st.y_total = off;
+    st.s_off.assign(n, 0);
+    st.s_size.assign(n, 0);
+    off = 0;
+    for (int k = 0; k < n; ++k) {
+      const long long left = (k == 0) ? 1 : st.r[k - 1];
+      const long long right = (k == n - 1) ? 1 : st.r[k];
+      st.s_off[k] = off;
+      st.s_size[k] = left * st.d[k] * right;
+      off += st.s_size[k];
+    }
+    st.s_total = off;
+    st.r_off.assign(n, 0);
+    off = 0;
+    for (int k = 1; k <= n - 1; ++k) {
+      st.r_off[k] = off;
+      off += (long long)st.D[k] * st.D[k];
+    }
+    st.r_total = off;
+    tn_plan_t tmp;
+    tmp.steps.push_back(st);
+    const Dims dm = plan_dims(&tmp);
+    // carve the static array: boundary sites, blocks, R_k, X, M, G, L, P, eigenvalues,
+    // max-abs slots, log-scale and status per instance
+    const long long B = n_inst;
+    const size_t dbl = sizeof(double);
+    const size_t parts[] = {dbl * size_t(dm.maxS * B),   dbl * size_t(dm.maxY * B),
+                            dbl * size_t(dm.maxR * B),   dbl * size_t(dm.maxX * B),
+                            dbl * size_t(dm.maxM * B),   dbl * size_t(dm.maxM * B),
+                            dbl * size_t(dm.maxL * B),   dbl * size_t(dm.maxP * B),
+                            dbl * size_t(dm.maxLam * B), sizeof(unsigned long long) * size_t(dm.maxN * B),
+                            dbl * size_t(B),             sizeof(int) * size_t(B)};
+    size_t offs[12], need = 0;
+    for (int i = 0; i < 12; ++i) {
+      offs[i] = need;
+      need += align256(parts[i]);
+    }
+    if (need > TN_NOALLOC_SCRATCH_BYTES)
+      fail(TN_ERR_INVALID, "problem needs " + std::to_string(need) +
+                               " bytes of workspace; the static workspace holds " +
+                               std::to_string(size_t(TN_NOALLOC_SCRATCH_BYTES)));
+    int dev = 0;
+    ck(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) fail(TN_ERR_INVALID, "device ordinal out of range");
+    void* base_v = nullptr;
+    {
+      std::lock_guard<std::mutex> lock(g_noalloc_mu);
+      if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        ck(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress");
+        ck(tn::eigh_configure(), "eigh configure");
+        g_noalloc_addr[dev] = p;
+      }
+      base_v = g_noalloc_addr[dev];
+    }
+    char* base = static_cast<char*>(base_v);
+    Ws w{};
+    w.sS = dm.maxS; w.sY = dm.maxY; w.sR = dm.maxR; w.sX = dm.maxX; w.sM = dm.maxM;
+    w.sL = dm.maxL; w.sP = dm.maxP; w.sLam = dm.maxLam; w.sAmax = dm.maxN; w.sInv = 0;
+    w.S0 = nullptr;
+    w.inv = nullptr;
+    w.S1 = reinterpret_cast<double*>(base + offs[0]);
+    w.Y = reinterpret_cast<double*>(base + offs[1]);
+    w.R = reinterpret_cast<double*>(base + offs[2]);
+    w.X = reinterpret_cast<double*>(base + offs[3]);
+    w.M = reinterpret_cast<double*>(base + offs[4]);
+    w.G = reinterpret_cast<double*>(base + offs[5]);
+    w.L = reinterpret_cast<double*>(base + offs[6]);
+    w.P = reinterpret_cast<double*>(base + offs[7]);
+    w.lam = reinterpret_cast<double*>(base + offs[8]);
+    w.amax = reinterpret_cast<unsigned long long*>(base + offs[9]);
+    // a ctx that owns no device memory, pointing at the static workspace
+    tn_ctx local;
+    local.device = dev;
+    local.logscale = reinterpret_cast<double*>(base + offs[10]);
+    local.status = reinterpret_cast<int*>(base + offs[11]);
+    cudaStream_t strm = static_cast<cudaStream_t>(stream);
+    // the array keeps the previous call's contents: reset what starts at zero
+    ck(cudaMemsetAsync(local.logscale, 0, dbl * size_t(B), strm), "memset");
+    ck(cudaMemsetAsync(local.status, 0, sizeof(int) * size_t(B), strm), "memset");
+    for (int i = 0; i < n_inst; ++i)
+      ck(cudaMemcpyAsync(w.Y + w.sY * i, blocks_dev[i], dbl * st.y_total,
+                         cudaMemcpyDeviceToDevice, strm),
+         "copy blocks");
+    dm_pass(&local, st, w, w.S1, n_inst, TN_PREC_FP64, strm);
+    for (int i = 0; i < n_inst; ++i)
+      ck(cudaMemcpyAsync(tree_dev[i], w.S1 + w.sS * i + st.s_off[1],
+                         dbl * (st.s_total - st.s_size[0]), cudaMemcpyDeviceToDevice, strm),
+         "copy tree");
+    ck(cudaMemcpyAsync(lognorm_dev, local.logscale, dbl * size_t(B), cudaMemcpyDeviceToDevice,
+                       strm),
+       "copy lognorm");
+    ck(cudaMemcpyAsync(status_dev, local.status, sizeof(int) * size_t(B),
+                       cudaMemcpyDeviceToDevice, strm),
        "copy status");
     for (int k = 0; k < n - 1; ++k) ranks_host[k] = st.r[k];
   });
