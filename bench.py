@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "tf32fast", "bf16"])
+    p.add_argument("--precision", default="tf32", choices=["fp64", "tf32", "tf32fast", "bf16"])
     p.add_argument("--chi", type=int, default=64)
     p.add_argument("--size", type=int, default=32)
     p.add_argument("--batch", type=int, default=304)
@@ -342,6 +342,21 @@ def bench_ours(args):
                 "frac": achieved / peak, "traffic": traffic, "kernel_class": dom,
                 "launches": n_l, "ms_per_batch": ms, "peak_source": note,
                 "class_ms": {k: round(v[1], 3) for k, v in prof.items()}}
+    # the density-matrix contractions (env, local, density, projection) as one
+    # group: algorithmic flops over their summed event-timed duration
+    dm_cls = ("env", "local", "density", "project")
+    dm_ms = sum(prof[k][1] for k in dm_cls)
+    dm_flops = sum(flops[k] for k in dm_cls) * Bn
+    if prec == B.TN_PREC_FP64:
+        dm_peak, dm_note = FP64_ALU_TFLOPS, "FP64 ALU (no tensor cores)"
+    else:
+        bf16 = pk.get("bf16_tflops_sustained", FALLBACK["bf16_tflops_sustained"])
+        dm_peak = bf16 * TF32_PER_BF16
+        dm_note = f"{pk_src} bf16 sustained x 1.1/2.25 (tf32)"
+    dm_group = {"achieved": dm_flops / (dm_ms / 1e3) / 1e12, "peak": dm_peak, "unit": "TFLOP/s",
+                "frac": dm_flops / (dm_ms / 1e3) / 1e12 / dm_peak, "ms_per_batch": dm_ms,
+                "peak_source": dm_note,
+                "note": "algorithmic flops; the compensated TF32 split issues 3 MMAs per product"}
 
     out = {
         "metric": "approx contractions/s", "value": value, "unit": "contractions/s",
@@ -352,7 +367,8 @@ def bench_ours(args):
         "config": {"workload": WORKLOAD, "size": args.size, "chi": args.chi, "batch": Bn,
                    "precision": args.precision, "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"instances x{world}"},
-        "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline, "clocks": clocks,
+        "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline,
+        "density_matrix_contractions": dm_group, "clocks": clocks,
         "status_ok": int((status == 0).sum()),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

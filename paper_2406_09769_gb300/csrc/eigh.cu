@@ -352,6 +352,382 @@ __global__ void __launch_bounds__(kThreads) k_eigh_top(const T* __restrict__ Lg,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Register-resident variant for n <= 128, r <= 64 (the shapes of the MPS-tree
+// density matrices at chi <= 64).  Same mathematics as k_eigh_top; the work is
+// laid out so that barriers are few and every thread is busy:
+//   * Householder step: warp 0 forms the reflector; the 256 threads split the
+//     trailing matrix by (row, half of the columns) for the product A22 v and
+//     the rank-2 update (shared-memory rows of n + 1 words: no bank conflicts);
+//     four barriers per step;
+//   * eigenvalues: 4 threads per eigenvalue evaluate Sturm counts at 4 interior
+//     points of the current interval (multisection), a fixed number of rounds;
+//   * eigenvectors of T: inverse iteration, one thread per vector;
+//   * the r vectors are then held in registers by thread quads (column c,
+//     quarter q of its rows), so modified Gram-Schmidt needs two barriers per
+//     vector and the back-transformation H_0 ... H_{n-3} Z none at all.
+constexpr int kQ = 32;  // rows per quarter (n <= 128)
+
+template <typename T>
+__device__ __forceinline__ T fdiv(T a, T b) { return a / b; }
+template <>
+__device__ __forceinline__ float fdiv<float>(float a, float b) { return __fdividef(a, b); }
+
+// Sum over the 4 lanes of a thread quad; only those lanes need to be active.
+template <typename T>
+__device__ __forceinline__ T quad_sum(T v) {
+  const unsigned qm = 0xFu << (threadIdx.x & 28);
+  v += __shfl_xor_sync(qm, v, 1);
+  v += __shfl_xor_sync(qm, v, 2);
+  return v;
+}
+
+template <typename T>
+__device__ int sturm_count_fast(const T* dd, const T* e2, int n, T x, T pivmin) {
+  T q = dd[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  int c = (q < T(0));
+  for (int j = 1; j < n; ++j) {
+    q = dd[j] - x - fdiv(e2[j - 1], q);
+    if (fabs(q) < pivmin) q = -pivmin;
+    c += (q < T(0));
+  }
+  return c;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg, long long sL,
+                                                        T* __restrict__ Ug, long long sU,
+                                                        T* __restrict__ Utg, long long sUt,
+                                                        double* __restrict__ lamg, long long slam,
+                                                        int n, int r, int nlam, int* status) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  __shared__ T scal[8];
+  const int ld = n + 1;
+  const int nl = (nlam > r) ? nlam : r;
+  T* A = reinterpret_cast<T*>(raw);  // n x ld
+  T* Zs = A + n * ld;                 // r vectors of length n (column-major)
+  T* dd = Zs + r * n;
+  T* ee = dd + kNmax;
+  T* e2 = ee + kNmax;
+  T* tau = e2 + kNmax;
+  T* vb = tau + kNmax;
+  T* wv = vb + kNmax;
+  T* part = wv + kNmax;               // 2 x 128
+  T* lam = part + 2 * kNmax;          // kNmax
+  T* shift = lam + kNmax;             // 64
+  T* pub = shift + 64;                // kNmax
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int b = blockIdx.x;
+  const T* L = Lg + (long long)b * sL;
+
+  bool bad = false;
+  for (int idx = tid; idx < n * n; idx += kThreads) {
+    const int a = idx / n, c = idx % n;
+    const T x = T(0.5) * (L[(long long)a * n + c] + L[(long long)c * n + a]);
+    if (!isfinite(x)) bad = true;
+    A[a * ld + c] = x;
+  }
+  if (__syncthreads_or(bad)) {
+    for (int idx = tid; idx < n * r; idx += kThreads) Ug[(long long)b * sU + idx] = T(0);
+    if (Utg)
+      for (int idx = tid; idx < n * r; idx += kThreads) Utg[(long long)b * sUt + idx] = T(0);
+    if (tid == 0) status[b] = TN_ERR_NONFINITE;
+    return;
+  }
+
+  // ---- 1. Householder tridiagonalisation
+  const int ri = tid & 127, half = tid >> 7;
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;
+    if (warp == 0) {
+      T s = T(0);
+      for (int j = 1 + lane; j < m; j += 32) {
+        const T x = A[(k + 1 + j) * ld + k];
+        s += x * x;
+      }
+      s = warp_sum(s);
+      const T alpha = A[(k + 1) * ld + k];
+      T tk, beta, sc;
+      if (s == T(0)) {
+        tk = T(0); beta = alpha; sc = T(0);
+      } else {
+        beta = -copysign(sqrt(alpha * alpha + s), alpha);
+        tk = (beta - alpha) / beta;
+        sc = T(1) / (alpha - beta);
+      }
+      for (int j = lane; j < m; j += 32) {
+        const T x = (j == 0) ? T(1) : (tk == T(0) ? T(0) : A[(k + 1 + j) * ld + k] * sc);
+        vb[j] = x;
+        A[(k + 1 + j) * ld + k] = x;
+      }
+      if (lane == 0) {
+        dd[k] = A[k * ld + k];
+        ee[k] = beta;
+        tau[k] = tk;
+      }
+    }
+    __syncthreads();
+    const T tk = tau[k];
+    if (tk == T(0)) continue;  // uniform across the block
+    const int c0 = half ? (m + 1) / 2 : 0, c1 = half ? m : (m + 1) / 2;
+    if (ri < m) {
+      const T* row = A + (k + 1 + ri) * ld + (k + 1);
+      T s0 = T(0), s1 = T(0);
+      int c = c0;
+      for (; c + 1 < c1; c += 2) {
+        s0 += row[c] * vb[c];
+        s1 += row[c + 1] * vb[c + 1];
+      }
+      if (c < c1) s0 += row[c] * vb[c];
+      part[half * kNmax + ri] = s0 + s1;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      T d = T(0);
+      for (int i = lane; i < m; i += 32) {
+        const T wi = tk * (part[i] + part[kNmax + i]);
+        wv[i] = wi;
+        d += vb[i] * wi;
+      }
+      d = warp_sum(d);
+      const T K = T(-0.5) * tk * d;
+      for (int i = lane; i < m; i += 32) wv[i] += K * vb[i];
+    }
+    __syncthreads();
+    if (ri < m) {
+      const T vi = vb[ri], wi = wv[ri];
+      T* row = A + (k + 1 + ri) * ld + (k + 1);
+      for (int c = c0; c < c1; ++c) row[c] -= vi * wv[c] + wi * vb[c];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (n >= 2) {
+      dd[n - 2] = A[(n - 2) * ld + (n - 2)];
+      ee[n - 2] = A[(n - 1) * ld + (n - 2)];
+      tau[n - 2] = T(0);
+    }
+    dd[n - 1] = A[(n - 1) * ld + (n - 1)];
+    ee[n - 1] = T(0);
+    T gl = dd[0], gu = dd[0], emax = T(0);
+    for (int j = 0; j < n; ++j) {
+      const T el = (j > 0) ? fabs(ee[j - 1]) : T(0);
+      const T er = (j + 1 < n) ? fabs(ee[j]) : T(0);
+      gl = fmin(gl, dd[j] - el - er);
+      gu = fmax(gu, dd[j] + el + er);
+      if (j + 1 < n) {
+        e2[j] = ee[j] * ee[j];
+        emax = fmax(emax, e2[j]);
+      }
+    }
+    const T tnorm = fmax(fabs(gl), fabs(gu));
+    const T eps = Lim<T>::eps();
+    const T pivmin = Lim<T>::safmin() * fmax(T(1), emax);
+    gl -= T(2.1) * tnorm * eps * n + T(4.2) * pivmin;
+    gu += T(2.1) * tnorm * eps * n + T(4.2) * pivmin;
+    scal[1] = gl;
+    scal[2] = gu;
+    scal[3] = tnorm;
+    scal[4] = pivmin;
+  }
+  __syncthreads();
+  const T gl = scal[1], gu = scal[2], tnorm = scal[3], pivmin = scal[4];
+  const T eps = Lim<T>::eps();
+
+  // ---- 2. multisection: 4 threads per eigenvalue, interval shrinks 5x per round
+  {
+    const int q = tid & 3;
+    const int rounds = (sizeof(T) == 8) ? 24 : 12;
+    for (int base = 0; base < nl; base += kThreads / 4) {
+      const int t = base + (tid >> 2);
+      const bool valid = (t < nl) && (t < n);
+      const int j = n - 1 - t;
+      T lo = gl, hi = gu;
+      for (int it = 0; it < rounds; ++it) {
+        const T h = (hi - lo) / T(5);
+        const T x = lo + h * T(q + 1);
+        const int cnt = valid ? sturm_count_fast(dd, e2, n, x, pivmin) : 0;
+        const int qb = lane & ~3;
+        const int n0 = __shfl_sync(0xffffffffu, cnt, qb);
+        const int n1 = __shfl_sync(0xffffffffu, cnt, qb + 1);
+        const int n2 = __shfl_sync(0xffffffffu, cnt, qb + 2);
+        const int n3 = __shfl_sync(0xffffffffu, cnt, qb + 3);
+        const T x0 = lo + h, x1 = lo + h * T(2), x2 = lo + h * T(3), x3 = lo + h * T(4);
+        if (n0 > j) { hi = x0; }
+        else if (n1 > j) { lo = x0; hi = x1; }
+        else if (n2 > j) { lo = x1; hi = x2; }
+        else if (n3 > j) { lo = x2; hi = x3; }
+        else { lo = x3; }
+      }
+      if (valid && q == 0) lam[t] = T(0.5) * (lo + hi);
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const T pertol = T(10) * eps * fmax(tnorm, Lim<T>::safmin());
+    for (int t = 0; t < r; ++t) {
+      T s = lam[t];
+      if (t > 0 && shift[t - 1] - s < pertol) s = shift[t - 1] - pertol;
+      shift[t] = s;
+    }
+  }
+  __syncthreads();
+
+  // ---- 3. inverse iteration (2 sweeps), one thread per eigenvector
+  if (tid < r) {
+    T u1[kNmax], u2[kNmax], u3[kNmax], ml[kNmax], x[kNmax];
+    unsigned char pv[kNmax];
+    const T lmb = shift[tid];
+    const T tp = fmax(eps * tnorm, Lim<T>::safmin());
+    T a = dd[0] - lmb;
+    T bb = (n > 1) ? ee[0] : T(0);
+    for (int k = 0; k + 1 < n; ++k) {
+      const T c = ee[k];
+      const T nd = dd[k + 1] - lmb;
+      const T ns = (k + 2 < n) ? ee[k + 1] : T(0);
+      if (fabs(a) >= fabs(c)) {
+        if (a == T(0)) a = tp;
+        const T mlt = c / a;
+        pv[k] = 0; ml[k] = mlt; u1[k] = a; u2[k] = bb; u3[k] = T(0);
+        a = nd - mlt * bb;
+        bb = ns;
+      } else {
+        const T mlt = a / c;
+        pv[k] = 1; ml[k] = mlt; u1[k] = c; u2[k] = nd; u3[k] = ns;
+        a = bb - mlt * nd;
+        bb = -mlt * ns;
+      }
+    }
+    if (a == T(0)) a = tp;
+    u1[n - 1] = a;
+    for (int k = 0; k < n; ++k) {
+      unsigned int h = 2654435761u * (unsigned)(k + 1) ^ (40503u * (unsigned)(tid + 7));
+      h ^= h >> 13; h *= 0x5bd1e995u; h ^= h >> 15;
+      x[k] = T(1) + T(0.5) * (T(h & 0xffff) / T(65536) - T(0.5));
+    }
+    for (int it = 0; it < 2; ++it) {
+      for (int k = 0; k + 1 < n; ++k) {
+        if (pv[k]) { const T t = x[k]; x[k] = x[k + 1]; x[k + 1] = t; }
+        x[k + 1] -= ml[k] * x[k];
+      }
+      x[n - 1] = x[n - 1] / u1[n - 1];
+      if (n >= 2) x[n - 2] = (x[n - 2] - u2[n - 2] * x[n - 1]) / u1[n - 2];
+      for (int k = n - 3; k >= 0; --k) x[k] = (x[k] - u2[k] * x[k + 1] - u3[k] * x[k + 2]) / u1[k];
+      T mx = T(0);
+      for (int k = 0; k < n; ++k) mx = fmax(mx, fabs(x[k]));
+      const T inv = (mx > T(0) && isfinite(mx)) ? T(1) / mx : T(1);
+      for (int k = 0; k < n; ++k) x[k] *= inv;
+    }
+    T* zc = Zs + tid * n;
+    for (int k = 0; k < n; ++k) zc[k] = x[k];
+  }
+  __syncthreads();
+
+  // ---- 4. vectors into registers: thread = (column c, quarter q of the rows)
+  const int col = tid >> 2, qr = tid & 3;
+  const bool live = col < r;
+  T z[kQ];
+#pragma unroll
+  for (int kk = 0; kk < kQ; ++kk) {
+    const int row = qr * kQ + kk;
+    z[kk] = (live && row < n) ? Zs[col * n + row] : T(0);
+  }
+  // modified Gram-Schmidt in descending eigenvalue order
+  for (int j = 0; j < r; ++j) {
+    if (col == j) {
+      T s = T(0);
+#pragma unroll
+      for (int kk = 0; kk < kQ; ++kk) s += z[kk] * z[kk];
+      s = quad_sum(s);
+      const T inv = (s > T(0)) ? T(1) / sqrt(s) : T(0);
+#pragma unroll
+      for (int kk = 0; kk < kQ; ++kk) {
+        z[kk] *= inv;
+        pub[qr * kQ + kk] = z[kk];
+      }
+    }
+    __syncthreads();
+    if (live && col > j) {
+      T d = T(0);
+#pragma unroll
+      for (int kk = 0; kk < kQ; ++kk) d += pub[qr * kQ + kk] * z[kk];
+      d = quad_sum(d);
+#pragma unroll
+      for (int kk = 0; kk < kQ; ++kk) z[kk] -= d * pub[qr * kQ + kk];
+    }
+    __syncthreads();
+  }
+  // back-transformation by the stored reflectors (v_k in column k below the diagonal)
+  for (int k = n - 3; k >= 0; --k) {
+    const T tk = tau[k];
+    if (tk == T(0)) continue;
+    T vk[kQ];
+    T d = T(0);
+#pragma unroll
+    for (int kk = 0; kk < kQ; ++kk) {
+      const int row = qr * kQ + kk;
+      vk[kk] = (row > k && row < n) ? A[row * ld + k] : T(0);
+      d += vk[kk] * z[kk];
+    }
+    d = quad_sum(d) * tk;
+#pragma unroll
+    for (int kk = 0; kk < kQ; ++kk) z[kk] -= d * vk[kk];
+  }
+  // sign: largest-|.| entry (first on ties) positive
+  {
+    T best = T(-1);
+    int bi = kNmax;
+#pragma unroll
+    for (int kk = 0; kk < kQ; ++kk) {
+      const int row = qr * kQ + kk;
+      const T a = fabs(z[kk]);
+      if (row < n && (a > best || (a == best && row < bi))) { best = a; bi = row; }
+    }
+    const unsigned qm = 0xFu << (threadIdx.x & 28);
+    for (int o = 1; o <= 2; o <<= 1) {
+      const T ob = __shfl_xor_sync(qm, best, o);
+      const int oi = __shfl_xor_sync(qm, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    // the owner of row bi tells the quad its sign
+    T sv = T(0);
+#pragma unroll
+    for (int kk = 0; kk < kQ; ++kk)
+      if (qr * kQ + kk == bi) sv = z[kk];
+    sv = quad_sum(sv);
+    const T sgn = (sv < T(0)) ? T(-1) : T(1);
+#pragma unroll
+    for (int kk = 0; kk < kQ; ++kk) z[kk] *= sgn;
+  }
+  if (live) {
+    T* U = Ug + (long long)b * sU;
+#pragma unroll
+    for (int kk = 0; kk < kQ; ++kk) {
+      const int row = qr * kQ + kk;
+      if (row < n) U[(long long)row * r + col] = z[kk];
+    }
+    if (Utg) {
+      T* Ut = Utg + (long long)b * sUt + (long long)col * n;
+#pragma unroll
+      for (int kk = 0; kk < kQ; ++kk) {
+        const int row = qr * kQ + kk;
+        if (row < n) Ut[row] = z[kk];
+      }
+    }
+  }
+  if (lamg) {
+    double* lo = lamg + (long long)b * slam;
+    for (int t = tid; t < nlam && t < n; t += kThreads) lo[t] = double(lam[t]);
+  }
+}
+
+template <typename T>
+size_t eigh_fast_smem_bytes(int n, int r) {
+  // A, Z, then dd ee e2 tau vb wv (6), part (2), lam (1), shift (64), pub (1)
+  return sizeof(T) * (size_t(n) * (n + 1) + size_t(r) * n + 10 * kNmax + 64);
+}
+
 }  // namespace
 
 template <typename T>
@@ -365,6 +741,12 @@ cudaError_t launch_eigh_top(const T* L, long long sL, T* U, long long sU, T* Ut,
                             double* lam, long long slam, int n, int r, int nlam, int* status,
                             int batch, cudaStream_t st) {
   if (n < 1 || n > kNmax || r < 1 || r > n || nlam > n) return cudaErrorInvalidValue;
+  const size_t fast_smem = eigh_fast_smem_bytes<T>(n, r);
+  if (r <= 64 && fast_smem <= eigh_fast_smem_limit<T>()) {
+    k_eigh_fast<T><<<batch, kThreads, fast_smem, st>>>(L, sL, U, sU, Ut, sUt, lam, slam, n, r,
+                                                       nlam, status);
+    return cudaGetLastError();
+  }
   const size_t smem = eigh_smem_bytes<T>(n, r, nlam);
   if (smem > eigh_smem_limit<T>()) return cudaErrorInvalidValue;
   k_eigh_top<T, T><<<batch, kThreads, smem, st>>>(L, sL, U, sU, Ut, sUt, lam, slam, n, r, nlam,
@@ -373,22 +755,21 @@ cudaError_t launch_eigh_top(const T* L, long long sL, T* U, long long sU, T* Ut,
 }
 
 namespace {
-size_t g_limit[2] = {0, 0};
+size_t g_limit[4] = {0, 0, 0, 0};  // top<double>, top<float>, fast<double>, fast<float>
 
-template <typename T>
-cudaError_t configure_one(int slot) {
+template <typename K>
+cudaError_t configure_kernel(K kern, size_t* out) {
   int dev = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
   cudaFuncAttributes fa{};
-  e = cudaFuncGetAttributes(&fa, k_eigh_top<T, T>);
+  e = cudaFuncGetAttributes(&fa, kern);
   if (e != cudaSuccess) return e;
   const size_t lim = size_t(optin) - fa.sharedSizeBytes;
-  e = cudaFuncSetAttribute(k_eigh_top<T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           int(lim));
-  if (e == cudaSuccess) g_limit[slot] = lim;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(lim));
+  if (e == cudaSuccess) *out = lim;
   return e;
 }
 }  // namespace
@@ -397,13 +778,21 @@ template <typename T>
 size_t eigh_smem_limit() {
   return g_limit[sizeof(T) == 8 ? 0 : 1];
 }
+template <typename T>
+size_t eigh_fast_smem_limit() {
+  return g_limit[sizeof(T) == 8 ? 2 : 3];
+}
 template size_t eigh_smem_limit<double>();
 template size_t eigh_smem_limit<float>();
+template size_t eigh_fast_smem_limit<double>();
+template size_t eigh_fast_smem_limit<float>();
 
 cudaError_t eigh_configure() {
-  cudaError_t e = configure_one<double>(0);
-  if (e != cudaSuccess) return e;
-  return configure_one<float>(1);
+  cudaError_t e = configure_kernel(k_eigh_top<double, double>, &g_limit[0]);
+  if (e == cudaSuccess) e = configure_kernel(k_eigh_top<float, float>, &g_limit[1]);
+  if (e == cudaSuccess) e = configure_kernel(k_eigh_fast<double>, &g_limit[2]);
+  if (e == cudaSuccess) e = configure_kernel(k_eigh_fast<float>, &g_limit[3]);
+  return e;
 }
 
 template size_t eigh_smem_bytes<double>(int, int, int);

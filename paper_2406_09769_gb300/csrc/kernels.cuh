@@ -100,6 +100,8 @@ template <typename T>
 size_t eigh_smem_bytes(int n, int r, int nlam);
 template <typename T>
 size_t eigh_smem_limit();
+template <typename T>
+size_t eigh_fast_smem_limit();
 cudaError_t eigh_configure();
 
 }  // namespace tn
