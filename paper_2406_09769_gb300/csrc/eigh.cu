@@ -363,9 +363,11 @@ __global__ void __launch_bounds__(kThreads) k_eigh_top(const T* __restrict__ Lg,
 //   * eigenvalues: 4 threads per eigenvalue evaluate Sturm counts at 4 interior
 //     points of the current interval (multisection), a fixed number of rounds;
 //   * eigenvectors of T: inverse iteration, one thread per vector;
-//   * the r vectors are then held in registers by thread quads (column c,
-//     quarter q of its rows), so modified Gram-Schmidt needs two barriers per
-//     vector and the back-transformation H_0 ... H_{n-3} Z none at all.
+//   * the r vectors are then held in registers by thread quads (column c;
+//     thread q of the quad owns rows q, q+4, q+8, ... so that the quad's four
+//     reads of one shared-memory column fall in four banks), so modified
+//     Gram-Schmidt needs two barriers per vector and the back-transformation
+//     H_0 ... H_{n-3} Z none at all.
 constexpr int kQ = 32;  // rows per quarter (n <= 128)
 
 template <typename T>
@@ -407,7 +409,7 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
   const int nl = (nlam > r) ? nlam : r;
   T* A = reinterpret_cast<T*>(raw);  // n x ld
   T* Zs = A + n * ld;                 // r vectors of length n (column-major)
-  T* dd = Zs + r * n;
+  T* dd = Zs + r * (n + 1);          // Zs columns are padded to n + 1
   T* ee = dd + kNmax;
   T* e2 = ee + kNmax;
   T* tau = e2 + kNmax;
@@ -574,53 +576,74 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
   }
   __syncthreads();
 
-  // ---- 3. inverse iteration (2 sweeps), one thread per eigenvector
+  // ---- 3. inverse iteration, one thread per eigenvector: two solves of
+  // (T - lambda I) x = y with partial pivoting, the elimination applied to the
+  // right-hand side as the factorisation proceeds; the first from a fixed
+  // pseudo-random vector, the second from its normalised result, so the
+  // contamination by other eigenvectors falls like (eps ||T|| / gap)^2;
+  // clusters are separated by the Gram-Schmidt pass below.  y and x live in
+  // this thread's padded shared-memory column, the triangular factor in local
+  // memory.
+  const int zld = n + 1;
   if (tid < r) {
-    T u1[kNmax], u2[kNmax], u3[kNmax], ml[kNmax], x[kNmax];
-    unsigned char pv[kNmax];
+    T u1[kNmax], u2[kNmax], u3[kNmax];
+    T* y = Zs + tid * zld;
+    auto start = [&](int k) {
+      unsigned int h = 2654435761u * (unsigned)(k + 1) ^ (40503u * (unsigned)(tid + 7));
+      h ^= h >> 13; h *= 0x5bd1e995u; h ^= h >> 15;
+      return T(1) + T(0.5) * (T(h & 0xffff) / T(65536) - T(0.5));
+    };
     const T lmb = shift[tid];
     const T tp = fmax(eps * tnorm, Lim<T>::safmin());
+    for (int it = 0; it < 2; ++it) {
     T a = dd[0] - lmb;
     T bb = (n > 1) ? ee[0] : T(0);
+    T yk = (it == 0) ? start(0) : y[0];
     for (int k = 0; k + 1 < n; ++k) {
       const T c = ee[k];
       const T nd = dd[k + 1] - lmb;
       const T ns = (k + 2 < n) ? ee[k + 1] : T(0);
+      const T yn = (it == 0) ? start(k + 1) : y[k + 1];
       if (fabs(a) >= fabs(c)) {
         if (a == T(0)) a = tp;
-        const T mlt = c / a;
-        pv[k] = 0; ml[k] = mlt; u1[k] = a; u2[k] = bb; u3[k] = T(0);
+        const T mlt = fdiv(c, a);
+        u1[k] = a; u2[k] = bb; u3[k] = T(0);
+        y[k] = yk;
+        yk = yn - mlt * yk;
         a = nd - mlt * bb;
         bb = ns;
       } else {
-        const T mlt = a / c;
-        pv[k] = 1; ml[k] = mlt; u1[k] = c; u2[k] = nd; u3[k] = ns;
+        const T mlt = fdiv(a, c);
+        u1[k] = c; u2[k] = nd; u3[k] = ns;
+        y[k] = yn;
+        yk = yk - mlt * yn;
         a = bb - mlt * nd;
         bb = -mlt * ns;
       }
     }
     if (a == T(0)) a = tp;
     u1[n - 1] = a;
-    for (int k = 0; k < n; ++k) {
-      unsigned int h = 2654435761u * (unsigned)(k + 1) ^ (40503u * (unsigned)(tid + 7));
-      h ^= h >> 13; h *= 0x5bd1e995u; h ^= h >> 15;
-      x[k] = T(1) + T(0.5) * (T(h & 0xffff) / T(65536) - T(0.5));
+    T x2 = fdiv(yk, a);  // x_{k+2}, x_{k+1} rolling
+    y[n - 1] = x2;
+    T x1 = x2;
+    if (n >= 2) {
+      x1 = fdiv(y[n - 2] - u2[n - 2] * x2, u1[n - 2]);
+      y[n - 2] = x1;
     }
-    for (int it = 0; it < 2; ++it) {
-      for (int k = 0; k + 1 < n; ++k) {
-        if (pv[k]) { const T t = x[k]; x[k] = x[k + 1]; x[k + 1] = t; }
-        x[k + 1] -= ml[k] * x[k];
-      }
-      x[n - 1] = x[n - 1] / u1[n - 1];
-      if (n >= 2) x[n - 2] = (x[n - 2] - u2[n - 2] * x[n - 1]) / u1[n - 2];
-      for (int k = n - 3; k >= 0; --k) x[k] = (x[k] - u2[k] * x[k + 1] - u3[k] * x[k + 2]) / u1[k];
-      T mx = T(0);
-      for (int k = 0; k < n; ++k) mx = fmax(mx, fabs(x[k]));
-      const T inv = (mx > T(0) && isfinite(mx)) ? T(1) / mx : T(1);
-      for (int k = 0; k < n; ++k) x[k] *= inv;
+#pragma unroll 4
+    for (int k = n - 3; k >= 0; --k) {
+      const T xk = fdiv(y[k] - u2[k] * x1 - u3[k] * x2, u1[k]);
+      y[k] = xk;
+      x2 = x1;
+      x1 = xk;
     }
-    T* zc = Zs + tid * n;
-    for (int k = 0; k < n; ++k) zc[k] = x[k];
+    // the solve grows like 1 / (eps ||T||) and L_v carries an arbitrary
+    // overall scale: bring the vector to max-abs 1 before Gram-Schmidt squares it
+    T mx = T(0);
+    for (int k = 0; k < n; ++k) mx = fmax(mx, fabs(y[k]));
+    const T inv = (mx > T(0) && isfinite(mx)) ? T(1) / mx : T(1);
+    for (int k = 0; k < n; ++k) y[k] *= inv;
+    }  // two solves: contamination (eps ||T|| / gap)^2
   }
   __syncthreads();
 
@@ -630,8 +653,8 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
   T z[kQ];
 #pragma unroll
   for (int kk = 0; kk < kQ; ++kk) {
-    const int row = qr * kQ + kk;
-    z[kk] = (live && row < n) ? Zs[col * n + row] : T(0);
+    const int row = kk * 4 + qr;
+    z[kk] = (live && row < n) ? Zs[col * zld + row] : T(0);
   }
   // modified Gram-Schmidt in descending eigenvalue order
   for (int j = 0; j < r; ++j) {
@@ -644,17 +667,17 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
 #pragma unroll
       for (int kk = 0; kk < kQ; ++kk) {
         z[kk] *= inv;
-        pub[qr * kQ + kk] = z[kk];
+        pub[kk * 4 + qr] = z[kk];
       }
     }
     __syncthreads();
     if (live && col > j) {
       T d = T(0);
 #pragma unroll
-      for (int kk = 0; kk < kQ; ++kk) d += pub[qr * kQ + kk] * z[kk];
+      for (int kk = 0; kk < kQ; ++kk) d += pub[kk * 4 + qr] * z[kk];
       d = quad_sum(d);
 #pragma unroll
-      for (int kk = 0; kk < kQ; ++kk) z[kk] -= d * pub[qr * kQ + kk];
+      for (int kk = 0; kk < kQ; ++kk) z[kk] -= d * pub[kk * 4 + qr];
     }
     __syncthreads();
   }
@@ -666,7 +689,7 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
     T d = T(0);
 #pragma unroll
     for (int kk = 0; kk < kQ; ++kk) {
-      const int row = qr * kQ + kk;
+      const int row = kk * 4 + qr;
       vk[kk] = (row > k && row < n) ? A[row * ld + k] : T(0);
       d += vk[kk] * z[kk];
     }
@@ -680,7 +703,7 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
     int bi = kNmax;
 #pragma unroll
     for (int kk = 0; kk < kQ; ++kk) {
-      const int row = qr * kQ + kk;
+      const int row = kk * 4 + qr;
       const T a = fabs(z[kk]);
       if (row < n && (a > best || (a == best && row < bi))) { best = a; bi = row; }
     }
@@ -694,7 +717,7 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
     T sv = T(0);
 #pragma unroll
     for (int kk = 0; kk < kQ; ++kk)
-      if (qr * kQ + kk == bi) sv = z[kk];
+      if (kk * 4 + qr == bi) sv = z[kk];
     sv = quad_sum(sv);
     const T sgn = (sv < T(0)) ? T(-1) : T(1);
 #pragma unroll
@@ -704,14 +727,14 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
     T* U = Ug + (long long)b * sU;
 #pragma unroll
     for (int kk = 0; kk < kQ; ++kk) {
-      const int row = qr * kQ + kk;
+      const int row = kk * 4 + qr;
       if (row < n) U[(long long)row * r + col] = z[kk];
     }
     if (Utg) {
       T* Ut = Utg + (long long)b * sUt + (long long)col * n;
 #pragma unroll
       for (int kk = 0; kk < kQ; ++kk) {
-        const int row = qr * kQ + kk;
+        const int row = kk * 4 + qr;
         if (row < n) Ut[row] = z[kk];
       }
     }
@@ -725,7 +748,7 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
 template <typename T>
 size_t eigh_fast_smem_bytes(int n, int r) {
   // A, Z, then dd ee e2 tau vb wv (6), part (2), lam (1), shift (64), pub (1)
-  return sizeof(T) * (size_t(n) * (n + 1) + size_t(r) * n + 10 * kNmax + 64);
+  return sizeof(T) * (size_t(n) * (n + 1) + size_t(r) * (n + 1) + 10 * kNmax + 64);
 }
 
 }  // namespace

@@ -80,6 +80,59 @@ __global__ void __launch_bounds__(256) k_fuse_f32(const FuseSite* __restrict__ s
   }
 }
 
+// Same fusion, tiled for the transposed copy: block (32 x 8) owns a 32 x 32 tile
+// of Ymat[a'][j] (a' = a * dhl + hl, j = e * Dr + b * dhr + hr); Y is written
+// along j and Yt along a', both coalesced, through a shared-memory tile.
+// grid: (ceil(d*Dr / 32), ceil(Dl / 32), sites * batch), z = instance * sites + site.
+__global__ void __launch_bounds__(256) k_fuse_f32_tiled(const FuseSite* __restrict__ sites,
+                                                        int n_sites, const double* const* tens,
+                                                        const double* __restrict__ inv_norm,
+                                                        int nv, const float* __restrict__ S,
+                                                        long long sS, float* __restrict__ Y,
+                                                        long long sY, float* __restrict__ Yt,
+                                                        const int64_t* yt_off) {
+  __shared__ float tile[32][33];
+  const int site = blockIdx.z % n_sites, i = blockIdx.z / n_sites;
+  const FuseSite f = sites[site];
+  const int Dl = f.a * f.dhl, Dr = f.b * f.dhr, J = f.de * Dr;
+  const int j0 = blockIdx.x * 32, a0 = blockIdx.y * 32;
+  if (j0 >= J || a0 >= Dl) return;  // uniform per block
+  const double* Tb = tens[i] + f.t_off;
+  const float* Si = S + (long long)i * sS + f.s_off;
+  const double inv = inv_norm[(long long)i * nv + f.vertex];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int j = j0 + tx;
+  int e = 0, bb = 0, hr = 0;
+  if (j < J) {
+    e = j / Dr;
+    const int c = j - e * Dr;
+    bb = c / f.dhr;
+    hr = c - bb * f.dhr;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int ap = a0 + ty + 8 * q;
+    float v = 0.f;
+    if (j < J && ap < Dl) {
+      const int aa = ap / f.dhl, hl = ap - aa * f.dhl;
+      const double* T = Tb + hl * f.shl + hr * f.shr + e * f.se;
+      const float* Sk = Si + (long long)aa * f.dp * f.b + bb;
+      double acc = 0.0;
+      for (int p = 0; p < f.dp; ++p) acc = fma((double)Sk[(long long)p * f.b], T[p * f.sp], acc);
+      v = float(acc * inv);
+      Y[(long long)i * sY + f.y_off + (long long)ap * J + j] = v;
+    }
+    tile[ty + 8 * q][tx] = v;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int jj = j0 + ty + 8 * q, ap = a0 + tx;
+    if (jj < J && ap < Dl)
+      Yt[(long long)i * sY + yt_off[site] + (long long)jj * Dl + ap] = tile[tx][ty + 8 * q];
+  }
+}
+
 __global__ void k_fill_env_root_f32(float* R, long long sR, unsigned int* amax, long long s_amax,
                                     int batch) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -207,10 +260,17 @@ cudaError_t launch_sgemm_nt(const TcGemmArgs& g, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_fuse_f32(const FuseSite* sites, int n, int max_elems, const double* const* tens,
+cudaError_t launch_fuse_f32(const FuseSite* sites, int n, int max_elems, int max_dl, int max_j,
+                            const double* const* tens,
                             const double* inv_norm, int nv, const float* S, long long sS,
                             int trivial, float* Y, long long sY, float* Yt, const int64_t* yt_off,
                             int batch, cudaStream_t st) {
+  if (Yt && !trivial && max_dl > 0 && max_j > 0) {
+    dim3 grid((max_j + 31) / 32, (max_dl + 31) / 32, n * batch);
+    k_fuse_f32_tiled<<<grid, dim3(32, 8), 0, st>>>(sites, n, tens, inv_norm, nv, S, sS, Y, sY, Yt,
+                                                   yt_off);
+    return cudaGetLastError();
+  }
   dim3 grid((max_elems + 255) / 256, n, batch);
   k_fuse_f32<<<grid, 256, 0, st>>>(sites, tens, inv_norm, nv, S, sS, trivial, Y, sY, Yt, yt_off);
   return cudaGetLastError();
