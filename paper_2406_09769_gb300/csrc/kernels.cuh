@@ -53,7 +53,7 @@ struct TcGemmArgs {
 cudaError_t tc_gemm_configure();
 cudaError_t launch_sgemm_nt(const TcGemmArgs& g, cudaStream_t st);
 cudaError_t launch_tc_gemm(const TcGemmArgs& g, cudaStream_t st);
-size_t tc_gemm_smem_bytes(int BN, int split, int* stages_out);
+size_t tc_gemm_smem_bytes(int BN, int split, int K, int* stages_out);
 
 cudaError_t launch_site_norm(const double* const* tens, const int64_t* off, const int64_t* len,
                              int nv, int batch, double* inv_norm, double* logscale, int* status,

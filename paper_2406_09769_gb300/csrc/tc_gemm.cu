@@ -349,10 +349,15 @@ bool make_map(CUtensorMap* m, const float* ptr, int K, int rows, int batch, long
 
 }  // namespace
 
-size_t tc_gemm_smem_bytes(int BN, int split, int* stages_out) {
+size_t tc_gemm_smem_bytes(int BN, int split, int K, int* stages_out) {
+  // Stages are sized so that at least two CTAs share an SM (the per-instance
+  // tiles are small and latency-bound: co-resident CTAs hide each other's
+  // load and epilogue latency), and never exceed the number of K chunks.
   const size_t tile = size_t(128 + BN) * 128;
   const size_t stage = split ? 2 * tile : tile;
-  int stages = int((200 * 1024) / stage);
+  int stages = int((108 * 1024) / stage);
+  const int nk = (K + kChunk - 1) / kChunk;
+  if (stages > nk) stages = nk;
   if (stages > 4) stages = 4;
   if (stages < 1) stages = 1;
   if (stages_out) *stages_out = stages;
@@ -381,7 +386,7 @@ cudaError_t launch_tc_gemm(const TcGemmArgs& g, cudaStream_t st) {
   if (!make_map(&ma, g.A, g.K, g.M, g.batch, g.lda, g.sA, 128)) return cudaErrorInvalidValue;
   if (!make_map(&mb, g.B, g.K, g.N, g.batch, g.ldb, g.sB, BN)) return cudaErrorInvalidValue;
   int stages = 1;
-  const size_t smem = tc_gemm_smem_bytes(BN, g.split, &stages);
+  const size_t smem = tc_gemm_smem_bytes(BN, g.split, g.K, &stages);
   uint32_t cols = 32;
   while (cols < uint32_t(BN)) cols <<= 1;
   dim3 grid((g.N + BN - 1) / BN, (g.M + 127) / 128, g.batch);
