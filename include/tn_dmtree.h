@@ -160,8 +160,10 @@ tn_status tn_embed_tree(tn_ctx_t* ctx, int32_t n_inst, int32_t n_legs,
  * must be structurally identical (same graph shape, partition, path and
  * chi); instances differ in tensor data only.  sites_dev[i] is a device FP64
  * buffer with every site tensor of instance i packed at tn_plan_site_offset.
- * Asynchronous on stream; results are read with tn_logz.  learned_chi must
- * be 0 in this build.                                                       */
+ * Asynchronous on stream; results are read with tn_logz.  learned_chi = 0
+ * keeps each edge's plan rank r_k; learned_chi = 1 lets the rank model of
+ * ctx (tn_rank_model_load; TN_ERR_INVALID if none is loaded) choose a rank
+ * chi_k <= r_k per edge under a per-pass budget (see "learned ranks").     */
 tn_status tn_contract_approx(tn_ctx_t* ctx, const tn_plan_t* const* plans, int32_t n_inst,
                              const double* const* sites_dev, int32_t precision,
                              int32_t learned_chi, void* stream);
@@ -208,6 +210,86 @@ tn_status tn_embed_tree_noalloc(int32_t n_inst, int32_t n_legs, const int32_t* l
                                 int32_t chi, const int32_t* chi_per_edge,
                                 double* const* tree_dev, double* lognorm_dev,
                                 int32_t* status_dev, int32_t* ranks_host, void* stream);
+
+/* ---------------------------------------------------------- learned ranks
+ * The paper has no learned component: it truncates every edge to one chi.
+ * These calls let a small model spend a fixed rank budget unevenly.  After
+ * the eigensolve of tree vertex k of a DM pass, features of the spectrum of
+ * L_k (its eigenvalues, descending, over the effective dim A_k = chi_{k-1}
+ * d_k, the rows the ranks kept so far can fill) feed an MLP with BF16 weights
+ * and FP32 accumulation; chi_k = rint(64 y) clamped to [1, min(r_k, dim A_k,
+ * numerical rank)] (numerical rank: the last position whose eigenvalue is
+ * above 1e-12 lam_1), then lowered so that every later vertex u of the pass
+ * can still get rank min(2, r_u), within the pass budget sum_k min(
+ * chi_uniform, r_k) (the total rank of the uniform-chi_uniform method).  Columns of U_k beyond chi_k
+ * are zeroed: shapes stay those of the plan, the tree tensor network has rank
+ * chi_k on that edge.
+ *
+ * Features (22, in order): log10(lam_k / lam_1) / 30 for k = 2, 4, 8, 12, 16,
+ * 24, 32, 48, 64, 96, 128 (k clamped to dim A);
+ * log10(sum_{i >= r} lam_i / sum_i lam_i) / 30 for r = 8, 16, 24, 32, 48, 64
+ * (0 share when r >= dim A; negative lam count as 0); ratios and shares are
+ * floored at 1e-12;
+ * dim A / 128; k / (n - 1); pass index / number of DM passes; the pass
+ * budget not yet spent before vertex k / (n - 1 - k) (edges left, k's
+ * included) / 64; min(chi_uniform, r_k) / 64.  The last two use the
+ * chi_uniform of the last tn_rank_model_load (0 before any).
+ * Parameters (tn_rank_model_params() floats, in order): W1 (64 x 22,
+ * row-major), b1 (64), W2 (64 x 64), b2 (64), W3 (64), b3 (1); y = W3 .
+ * relu(W2 relu(W1 x + b1) + b2) + b3.                                       */
+
+/* Number of FP32 parameters of the rank model (5697).                     */
+int32_t tn_rank_model_params(void);
+
+/* Copies n_params FP32 parameters (host) into ctx, rounded to BF16, and sets
+ * the per-pass budget basis chi_uniform (>= 1).  Synchronous.  weights_host
+ * NULL unloads the model.                                                   */
+tn_status tn_rank_model_load(tn_ctx_t* ctx, const float* weights_host, int32_t n_params,
+                             int32_t chi_uniform);
+
+/* Spectrum records of later tn_contract_approx batches (device buffers owned
+ * by the caller, each may be NULL; all NULL turns recording off).  Edge e is
+ * the e-th eigensolve of a batch in launch order (pass by pass, vertex 1 to
+ * n-2 within a pass); for e < cap_edges and instance i of a batch of B:
+ * feat[(e B + i) 22 + j] the features, spec[(e B + i) 128 + j] the
+ * eigenvalues (zero beyond dim A), chi[e B + i] the rank kept.  acc[i] (B
+ * entries) receives sum_e of the discarded share sum_{j >= chi} lam_j /
+ * sum_j lam_j over all edges of the batch.  Recording does not change ranks
+ * unless learned_chi = 1.  The buffers must stay valid until tn_logz.      */
+tn_status tn_rank_record(tn_ctx_t* ctx, float* feat_dev, double* spec_dev, int32_t* chi_dev,
+                         double* acc_dev, int64_t cap_edges);
+
+/* Training labels: for every pass p (edges pass_start[p] .. pass_start[p+1]-1,
+ * at most 256 per pass; host array of n_pass + 1 entries, n_pass <= 65535)
+ * and instance i, greedy water-filling of the pass budget sum_e min(
+ * chi_uniform, cap[e]) over the pass's edges, each chi_e in [1, cap[e]] (cap
+ * host, n_edges entries: the plan ranks), minimising the summed discarded
+ * share of the recorded spectra spec (device, layout of tn_rank_record).
+ * Starting from 1 everywhere, each step raises the edge whose next
+ * eigenvalue has the largest share of its spectrum (ties: lowest edge).
+ * Writes chi_dev[e B + i] (device).  When feat_dev (device, layout of
+ * tn_rank_record) is set, features 20 and 21 of every edge are rewritten for
+ * the labelled allocation.  Synchronous.                                    */
+tn_status tn_rank_labels(tn_ctx_t* ctx, const double* spec_dev, int32_t n_inst,
+                         const int32_t* cap, const int32_t* pass_start, int32_t n_pass,
+                         int32_t chi_uniform, int32_t* chi_dev, float* feat_dev, void* stream);
+
+/* Mean squared error of the model (FP32 parameters w_dev, rounded to BF16 for
+ * the forward pass, as at inference) over samples idx_dev[0..n) (device; NULL
+ * = 0..n-1) of X_dev (rows of 22 features) against y_dev, and its gradient
+ * with respect to the rounded weights: loss_dev (1 float) and grad_dev
+ * (tn_rank_model_params floats) are overwritten.  Asynchronous.             */
+tn_status tn_rank_model_grad(tn_ctx_t* ctx, const float* X_dev, const float* y_dev,
+                             const int32_t* idx_dev, int32_t n, const float* w_dev,
+                             float* grad_dev, float* loss_dev, void* stream);
+
+/* steps Adam steps (beta 0.9, 0.999, eps 1e-8, learning rate lr) on w_dev
+ * (FP32 master weights, device, updated in place), step t using the
+ * minibatch idx_dev[t batch .. (t+1) batch) (device).  loss_dev[t] (device,
+ * steps floats) receives step t's minibatch loss.  Asynchronous.            */
+tn_status tn_rank_model_train(tn_ctx_t* ctx, const float* X_dev, const float* y_dev,
+                              const int32_t* idx_dev, int32_t steps, int32_t batch, float lr,
+                              float* w_dev, float* loss_dev, void* stream);
 
 /* ------------------------------------------------------------- diagnostics
  * Kernel classes of the hot path, for launch counts and timing.            */

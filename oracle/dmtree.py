@@ -139,7 +139,8 @@ def density_matrix_alg(blocks, chi, trace=None, force_branch=None):
             M = np.tensordot(P, blocks[v], axes=(1, 0)).reshape(P.shape[0] * d[v], -1)
         dimA, dimB = M.shape
         beyond = int(np.prod(d[v + 1:]))             # open legs on the parent side
-        r = min(chi, dimA, dimB, beyond)
+        chi_v = chi(v) if callable(chi) else chi     # per-edge ranks: chi(v)
+        r = min(chi_v, dimA, dimB, beyond)
         env = dm_parent[v]                           # L_u = dm(parent(v), v)
         direct = dimA <= dimB if force_branch is None else force_branch == "direct"
         if direct:
@@ -234,6 +235,10 @@ def partitioned_contract_rows(workload, chi, trace=None, force_branch=None):
     """ln Z of a 2D lattice network by Algorithm partitioned_contract with rows
     as partitions, the linear path and the MPS ansatz.
 
+    ``chi`` is one maximum rank, or a function chi(pass, v) giving the maximum
+    rank of tree vertex v in DM pass ``pass`` (0-based, one pass per absorbed
+    row) for per-edge ranks.
+
     Returns dict(logz, sign, logscale, steps) where steps lists the per-pass
     density_matrix_alg outputs when ``trace`` is a list (per-vertex records).
     """
@@ -253,7 +258,8 @@ def partitioned_contract_rows(workload, chi, trace=None, force_branch=None):
                 return dict(logz=float("nan"), sign=float(np.sign(s)), logscale=logscale)
             return dict(logz=float(np.log(s) + ls + logscale), sign=1.0, logscale=logscale)
         rec = [] if trace is not None else None
-        U, Mr, lognorm = density_matrix_alg(blocks, chi, trace=rec, force_branch=force_branch)
+        chi_pass = (lambda v, p=x - 1: chi(p, v)) if callable(chi) else chi
+        U, Mr, lognorm = density_matrix_alg(blocks, chi_pass, trace=rec, force_branch=force_branch)
         logscale += lognorm
         if trace is not None:
             trace.append(dict(row=x, vertices=rec, U=U, Mr=Mr, blocks=blocks))

@@ -56,6 +56,8 @@ _lib = None
 EXPORTS = ("tn_plan", "tn_plan_destroy", "tn_plan_query", "tn_plan_site_offset",
            "tn_ctx_create", "tn_ctx_destroy", "tn_embed_tree", "tn_contract_approx",
            "tn_logz", "tn_contract_approx_host", "tn_embed_tree_noalloc",
+           "tn_rank_model_params", "tn_rank_model_load", "tn_rank_record", "tn_rank_labels",
+           "tn_rank_model_grad", "tn_rank_model_train",
            "tn_ctx_set_profiling", "tn_ctx_profile", "tn_last_error")
 
 KERNEL_CLASSES = ("norm", "fuse", "env", "local", "density", "eig", "project", "root", "close")
@@ -88,6 +90,15 @@ def lib():
     L.tn_embed_tree_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p,
                                         ctypes.POINTER(_vp), ctypes.c_int32, _i32p,
                                         ctypes.POINTER(_vp), _vp, _vp, _i32p, _vp]
+    _f32p = ctypes.POINTER(ctypes.c_float)
+    L.tn_rank_model_params.argtypes = []
+    L.tn_rank_model_load.argtypes = [_vp, _f32p, ctypes.c_int32, ctypes.c_int32]
+    L.tn_rank_record.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int64]
+    L.tn_rank_labels.argtypes = [_vp, _vp, ctypes.c_int32, _i32p, _i32p, ctypes.c_int32,
+                                 ctypes.c_int32, _vp, _vp, _vp]
+    L.tn_rank_model_grad.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int32, _vp, _vp, _vp, _vp]
+    L.tn_rank_model_train.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_float, _vp, _vp, _vp]
     L.tn_ctx_set_profiling.argtypes = [_vp, ctypes.c_int32]
     L.tn_ctx_profile.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]
@@ -269,6 +280,48 @@ def tn_contract_approx_host(ctx, plans, sites_host, precision=TN_PREC_FP64, lear
     if st != TN_OK and (raise_on_error or st not in (4, 5)):
         _check(st, ctx)
     return logz, status
+
+
+def tn_rank_model_params():
+    return int(lib().tn_rank_model_params())
+
+
+def tn_rank_model_load(ctx, weights, chi_uniform):
+    """Load FP32 rank-model parameters (host array) or unload them (weights=None)."""
+    if weights is None:
+        _check(lib().tn_rank_model_load(ctx.handle, None, 0, int(chi_uniform)), ctx)
+        return
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    _check(lib().tn_rank_model_load(ctx.handle, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                    len(w), int(chi_uniform)), ctx)
+
+
+def tn_rank_record(ctx, feat_dev=0, spec_dev=0, chi_dev=0, acc_dev=0, cap_edges=0):
+    """Set (device addresses) or clear (all 0) the spectrum records of later batches."""
+    _check(lib().tn_rank_record(ctx.handle, _vp(int(feat_dev) or None), _vp(int(spec_dev) or None),
+                                _vp(int(chi_dev) or None), _vp(int(acc_dev) or None),
+                                int(cap_edges)), ctx)
+
+
+def tn_rank_labels(ctx, spec_dev, n_inst, cap, pass_start, chi_uniform, chi_dev, feat_dev=0,
+                   stream=0):
+    c, cp = _i32(cap)
+    ps, psp = _i32(pass_start)
+    _check(lib().tn_rank_labels(ctx.handle, _vp(int(spec_dev)), int(n_inst), cp, psp,
+                                len(ps) - 1, int(chi_uniform), _vp(int(chi_dev)),
+                                _vp(int(feat_dev) or None), _vp(int(stream))), ctx)
+
+
+def tn_rank_model_grad(ctx, X_dev, y_dev, n, w_dev, grad_dev, loss_dev, idx_dev=0, stream=0):
+    _check(lib().tn_rank_model_grad(ctx.handle, _vp(int(X_dev)), _vp(int(y_dev)),
+                                    _vp(int(idx_dev) or None), int(n), _vp(int(w_dev)),
+                                    _vp(int(grad_dev)), _vp(int(loss_dev)), _vp(int(stream))), ctx)
+
+
+def tn_rank_model_train(ctx, X_dev, y_dev, idx_dev, steps, batch, lr, w_dev, loss_dev, stream=0):
+    _check(lib().tn_rank_model_train(ctx.handle, _vp(int(X_dev)), _vp(int(y_dev)),
+                                     _vp(int(idx_dev)), int(steps), int(batch), float(lr),
+                                     _vp(int(w_dev)), _vp(int(loss_dev)), _vp(int(stream))), ctx)
 
 
 def tn_ctx_set_profiling(ctx, on):

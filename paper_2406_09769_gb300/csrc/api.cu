@@ -87,6 +87,18 @@ struct tn_ctx {
   };
   std::vector<Rec> recs;
   bool tc_ready = false;  // tcgen05/TMA path configured on this device
+  // learned per-edge rank allocation
+  DevBuf model_buf;        // BF16 MLP parameters
+  int chi_uniform = 0;
+  bool have_model = false;
+  DevBuf learn_buf;        // per-instance running budgets
+  float* rec_feat = nullptr;
+  double* rec_spec = nullptr;
+  int* rec_chi = nullptr;
+  double* rec_acc = nullptr;
+  int64_t rec_cap = 0;     // edges (eigensolves) the record buffers hold per instance
+  DevBuf train_buf;        // gradient and Adam moments
+  DevBuf aux_buf;          // label tables, sample indices
   // device pointers carved from `results`
   double* logz = nullptr;
   int* status = nullptr;
@@ -328,11 +340,87 @@ void gemm(tn_ctx* c, int cls, bool ta, bool tb, const double* A, long long sA, i
   ck(tn::launch_dgemm(ta, tb, g, st), "dgemm launch");
 }
 
+// Per-pass context of the learned rank allocation and of spectrum recording.
+struct PassCtx {
+  int pass = 0, npass = 1;
+  bool learned = false, record = false;
+  int budget_total = 0;
+  int* budget_rem = nullptr;
+  long long* edge = nullptr;  // running eigensolve index of the contraction
+};
+
+int pass_budget(const tn::Step& st, int chi_u) {
+  int b = 0;
+  for (int k = 1; k <= st.n - 2; ++k) b += std::min(chi_u, st.r[k]);
+  return b;
+}
+
+struct LearnState {
+  bool learned = false, record = false;
+  int* budget_rem = nullptr;
+  long long edge = 0;
+  int pass = 0, npass = 1;
+};
+
+LearnState learn_begin(tn_ctx* c, const tn_plan_t* P, int B, bool learned, cudaStream_t strm) {
+  LearnState s;
+  s.learned = learned;
+  s.record = c->rec_feat || c->rec_spec || c->rec_chi || c->rec_acc;
+  s.npass = std::max(1, int(P->info.n_dm_passes));
+  if (s.learned || s.record) {
+    s.budget_rem = static_cast<int*>(c->learn_buf.get(2 * sizeof(int) * size_t(B)));
+    if (c->rec_acc)
+      ck(cudaMemsetAsync(c->rec_acc, 0, sizeof(double) * size_t(B), strm), "memset acc");
+  }
+  return s;
+}
+
+PassCtx learn_pass(LearnState& s, tn_ctx* c, const tn::Step& st) {
+  PassCtx pc;
+  pc.pass = s.pass++;
+  pc.npass = s.npass;
+  pc.learned = s.learned;
+  pc.record = s.record;
+  pc.budget_total = c->chi_uniform > 0 ? pass_budget(st, c->chi_uniform) : 0;
+  pc.budget_rem = s.budget_rem;
+  pc.edge = &s.edge;
+  return pc;
+}
+
+// After the eigensolve of vertex k: learned rank (mask U beyond chi) and/or records.
+template <typename T>
+void rank_hook(tn_ctx* c, const PassCtx* pc, const tn::Step& st, int k, int A, int rk,
+               const double* lam, long long slam, T* U, long long sU, T* Ut, long long sUt, int B,
+               cudaStream_t strm) {
+  if (!pc || !(pc->learned || pc->record)) return;
+  Scope sc(c, TN_KC_EIG, strm);
+  tn::RankArgs g{};
+  g.lam = lam; g.slam = slam; g.A = A; g.rk = rk; g.dk = st.d[k];
+  g.v = k; g.nlegs = st.n; g.pass = pc->pass; g.npass = pc->npass;
+  g.model = pc->learned ? c->model_buf.p : nullptr;
+  g.budget_total = pc->budget_total;
+  g.chi_uniform = c->chi_uniform;
+  g.edges_after = st.n - 2 - k;
+  g.reserve_after = 0;
+  for (int u = k + 1; u <= st.n - 2; ++u) g.reserve_after += std::min(2, st.r[u]);
+  g.first = (k == 1);
+  g.budget_rem = pc->budget_rem;
+  g.prev_chi = pc->budget_rem + B;
+  g.acc = c->rec_acc;
+  const long long e = pc->edge ? (*pc->edge)++ : 0;
+  if (pc->record && e < c->rec_cap) {
+    g.rec_chi = c->rec_chi; g.rec_feat = c->rec_feat; g.rec_spec = c->rec_spec;
+    g.rec_off = e * B;
+  }
+  ck(tn::launch_rank_select<T>(g, U, sU, Ut, sUt, B, strm), "rank select");
+}
+
 // One density_matrix_alg pass (Sec. 5) over the blocks in w.Y (layout of st),
 // writing the tree TN as boundary sites into Snext (layout st.s_off).
 void dm_pass(tn_ctx* c, const tn::Step& st, const Ws& w, double* Snext, int B, int precision,
-             cudaStream_t strm) {
+             cudaStream_t strm, const PassCtx* pc = nullptr) {
   (void)precision;
+  const bool want_lam = pc && (pc->learned || pc->record);
   const int n = st.n;
   const auto& D = st.D;
   const auto& d = st.d;
@@ -371,9 +459,10 @@ void dm_pass(tn_ctx* c, const tn::Step& st, const Ws& w, double* Snext, int B, i
     // U_v = leading_eigenvectors(L_v, r_k), written as boundary site k
     double* Uk = Snext + st.s_off[k];
     Scope(c, TN_KC_EIG, strm),
-    ck(tn::launch_eigh_top<double>(w.L, w.sL, Uk, w.sS, nullptr, 0, w.lam, w.sLam, A, rk, 0,
-                                   c->status, B, strm),
+    ck(tn::launch_eigh_top<double>(w.L, w.sL, Uk, w.sS, nullptr, 0, w.lam, w.sLam, A, rk,
+                                   want_lam ? A : 0, c->status, B, strm),
        "eigh launch");
+    rank_hook<double>(c, pc, st, k, A, rk, w.lam, w.sLam, Uk, w.sS, nullptr, 0, B, strm);
     // P_v = U_v^T M_v  (rk x Dr)
     gemm(c, TN_KC_PROJECT, true, false, Uk, w.sS, rk, w.M, w.sM, Dr, w.P, w.sP, Dr, rk, Dr, A, B, nullptr, 0,
          nullptr, 0, strm);
@@ -387,10 +476,11 @@ void dm_pass(tn_ctx* c, const tn::Step& st, const Ws& w, double* Snext, int B, i
 }
 
 void run_plan(tn_ctx* c, const tn_plan_t* P, int B, const double* const* tens_dev, int precision,
-              cudaStream_t strm) {
+              bool learned, cudaStream_t strm) {
   const Dims dm = plan_dims(P);
   ensure_results(c, B);
   ck(cudaMemsetAsync(c->err_flag, 0, sizeof(int), strm), "memset err");
+  LearnState ls = learn_begin(c, P, B, learned, strm);
   const Ws w = carve(c, dm, B, P->n_vertices);
   const double** tens_table = nullptr;
   int64_t *off_dev = nullptr, *len_dev = nullptr;
@@ -422,7 +512,8 @@ void run_plan(tn_ctx* c, const tn_plan_t* P, int B, const double* const* tens_de
       ck(tn::launch_fuse(tabs[s].fuse, st.n, maxe, tens_table, w.inv, P->n_vertices, Scur, w.sS, 0,
                          w.Y, w.sY, B, strm),
          "fuse");
-      dm_pass(c, st, w, Snext, B, precision, strm);
+      const PassCtx pc = learn_pass(ls, c, st);
+      dm_pass(c, st, w, Snext, B, precision, strm, &pc);
       std::swap(Scur, Snext);
     } else {
       Scope(c, TN_KC_FUSE, strm),
@@ -531,7 +622,8 @@ void tgemm(tn_ctx* c, int cls, const float* A, long long sA, int lda, const floa
 
 // sub_split: compensated products also on the density-matrix side (env, L_v).
 void dm_pass_tc(tn_ctx* c, const tn::Step& st, const Lay& l, const WsF& w, float* Snext, int B,
-                int sub_split, cudaStream_t strm) {
+                int sub_split, cudaStream_t strm, const PassCtx* pc = nullptr) {
+  const bool want_lam = pc && (pc->learned || pc->record);
   const int n = st.n;
   const auto& D = st.D;
   const auto& d = st.d;
@@ -565,9 +657,10 @@ void dm_pass_tc(tn_ctx* c, const tn::Step& st, const Lay& l, const WsF& w, float
           B, nullptr, 0, nullptr, 0, sub_split, strm);
     float* Uk = Snext + l.s_off[k];
     Scope(c, TN_KC_EIG, strm),
-    ck(tn::launch_eigh_top<float>(w.L, w.sL, Uk, w.sS, w.Ut, w.sUt, w.lam, w.sLam, A, rk, 0,
-                                  c->status, B, strm),
+    ck(tn::launch_eigh_top<float>(w.L, w.sL, Uk, w.sS, w.Ut, w.sUt, w.lam, w.sLam, A, rk,
+                                  want_lam ? A : 0, c->status, B, strm),
        "eigh launch");
+    rank_hook<float>(c, pc, st, k, A, rk, w.lam, w.sLam, Uk, w.sS, w.Ut, w.sUt, B, strm);
     // P_v = U_v^T M_v (value path, compensated)
     tgemm(c, TN_KC_PROJECT, w.Ut, w.sUt, A, w.Mt, w.sM, A, w.P, w.sP, Dr, nullptr, 0, 0, 0, rk,
           Dr, A, B, nullptr, 0, nullptr, 0, 1, strm);
@@ -580,12 +673,13 @@ void dm_pass_tc(tn_ctx* c, const tn::Step& st, const Lay& l, const WsF& w, float
 }
 
 void run_plan_tc(tn_ctx* c, const tn_plan_t* P, int B, const double* const* tens_dev,
-                 int sub_split, cudaStream_t strm) {
+                 int sub_split, bool learned, cudaStream_t strm) {
   std::vector<Lay> lay;
   for (const tn::Step& st : P->steps) lay.push_back(lay_f32(st));
   ensure_results(c, B);
   ck(cudaMemsetAsync(c->err_flag, 0, sizeof(int), strm), "memset err");
   const WsF w = carve_f32(c, P, lay, B);
+  LearnState ls = learn_begin(c, P, B, learned, strm);
   const double** tens_table = nullptr;
   int64_t *off_dev = nullptr, *len_dev = nullptr;
   std::vector<StepTables> tabs =
@@ -617,7 +711,8 @@ void run_plan_tc(tn_ctx* c, const tn_plan_t* P, int B, const double* const* tens
                              P->n_vertices, Scur, w.sS, 0, w.Y, w.sY, w.Yt, tabs[s].y_off, B,
                              strm),
          "fuse");
-      dm_pass_tc(c, st, lay[s], w, Snext, B, sub_split, strm);
+      const PassCtx pc = learn_pass(ls, c, st);
+      dm_pass_tc(c, st, lay[s], w, Snext, B, sub_split, strm, &pc);
       std::swap(Scur, Snext);
     } else {
       Scope(c, TN_KC_FUSE, strm),
@@ -703,6 +798,10 @@ extern "C" tn_status tn_ctx_destroy(tn_ctx_t* c) {
   c->stage.release();
   c->tables.release();
   c->results.release();
+  c->model_buf.release();
+  c->learn_buf.release();
+  c->train_buf.release();
+  c->aux_buf.release();
   if (c->pinned) cudaFreeHost(c->pinned);
   if (c->pinned_free) cudaEventDestroy(c->pinned_free);
   delete c;
@@ -718,7 +817,8 @@ extern "C" tn_status tn_contract_approx(tn_ctx_t* c, const tn_plan_t* const* pla
   }
   return guarded(c, "tn_contract_approx", [&] {
     if (!plans || !sites_dev || n_inst < 1) fail(TN_ERR_INVALID, "plans/sites NULL or n_inst < 1");
-    if (learned_chi) fail(TN_ERR_UNSUPPORTED, "learned chi is not available in this build");
+    if (learned_chi && !c->have_model)
+      fail(TN_ERR_INVALID, "learned_chi = 1 needs a rank model (tn_rank_model_load)");
     for (int i = 0; i < n_inst; ++i) {
       if (!plans[i] || !sites_dev[i]) fail(TN_ERR_INVALID, "NULL plan or site buffer");
       if (!tn::plans_equivalent(plans[0], plans[i]))
@@ -727,12 +827,148 @@ extern "C" tn_status tn_contract_approx(tn_ctx_t* c, const tn_plan_t* const* pla
     ck(cudaSetDevice(c->device), "cudaSetDevice");
     cudaStream_t strm = static_cast<cudaStream_t>(stream);
     if (precision == TN_PREC_FP64) {
-      run_plan(c, plans[0], n_inst, sites_dev, precision, strm);
+      run_plan(c, plans[0], n_inst, sites_dev, precision, learned_chi != 0, strm);
     } else if (precision == TN_PREC_TF32 || precision == TN_PREC_TF32_FAST) {
       if (!c->tc_ready) fail(TN_ERR_UNSUPPORTED, "tcgen05 path unavailable on this device");
-      run_plan_tc(c, plans[0], n_inst, sites_dev, precision == TN_PREC_TF32 ? 1 : 0, strm);
+      run_plan_tc(c, plans[0], n_inst, sites_dev, precision == TN_PREC_TF32 ? 1 : 0,
+                  learned_chi != 0, strm);
     } else {
       fail(TN_ERR_UNSUPPORTED, "precision mode not implemented in this build");
+    }
+  });
+}
+
+extern "C" int32_t tn_rank_model_params(void) { return tn::rank_model_params(); }
+
+extern "C" tn_status tn_rank_model_load(tn_ctx_t* c, const float* weights_host, int32_t n_params,
+                                        int32_t chi_uniform) {
+  if (!c) {
+    tn::set_error("tn_rank_model_load: ctx is NULL");
+    return TN_ERR_INVALID;
+  }
+  return guarded(c, "tn_rank_model_load", [&] {
+    if (!weights_host) {
+      c->have_model = false;
+      return;
+    }
+    const int np = tn::rank_model_params();
+    if (n_params != np) fail(TN_ERR_INVALID, "n_params differs from tn_rank_model_params()");
+    if (chi_uniform < 1) fail(TN_ERR_INVALID, "chi_uniform must be >= 1");
+    ck(cudaSetDevice(c->device), "cudaSetDevice");
+    float* tmp = static_cast<float*>(c->train_buf.get(sizeof(float) * size_t(np)));
+    void* bf = c->model_buf.get(2 * size_t(np));
+    ck(cudaMemcpy(tmp, weights_host, sizeof(float) * size_t(np), cudaMemcpyHostToDevice),
+       "copy weights");
+    ck(tn::launch_to_bf16(tmp, bf, np, nullptr), "to bf16");
+    ck(cudaDeviceSynchronize(), "synchronize");
+    c->chi_uniform = chi_uniform;
+    c->have_model = true;
+  });
+}
+
+extern "C" tn_status tn_rank_record(tn_ctx_t* c, float* feat_dev, double* spec_dev,
+                                    int32_t* chi_dev, double* acc_dev, int64_t cap_edges) {
+  if (!c) {
+    tn::set_error("tn_rank_record: ctx is NULL");
+    return TN_ERR_INVALID;
+  }
+  return guarded(c, "tn_rank_record", [&] {
+    if (cap_edges < 0) fail(TN_ERR_INVALID, "cap_edges < 0");
+    c->rec_feat = feat_dev;
+    c->rec_spec = spec_dev;
+    c->rec_chi = chi_dev;
+    c->rec_acc = acc_dev;
+    c->rec_cap = cap_edges;
+  });
+}
+
+extern "C" tn_status tn_rank_labels(tn_ctx_t* c, const double* spec_dev, int32_t n_inst,
+                                    const int32_t* cap, const int32_t* pass_start,
+                                    int32_t n_pass, int32_t chi_uniform, int32_t* chi_dev,
+                                    float* feat_dev, void* stream) {
+  if (!c) {
+    tn::set_error("tn_rank_labels: ctx is NULL");
+    return TN_ERR_INVALID;
+  }
+  return guarded(c, "tn_rank_labels", [&] {
+    if (!spec_dev || !cap || !pass_start || !chi_dev || n_inst < 1 || n_pass < 1 ||
+        n_pass > 65535 || chi_uniform < 1)
+      fail(TN_ERR_INVALID, "invalid argument");
+    if (pass_start[0] != 0) fail(TN_ERR_INVALID, "pass_start[0] must be 0");
+    for (int p = 0; p < n_pass; ++p) {
+      const int ne = pass_start[p + 1] - pass_start[p];
+      if (ne < 1 || ne > tn::water_fill_max_edges())
+        fail(TN_ERR_INVALID, "a pass needs 1 .. 256 edges");
+    }
+    const int n_edges = pass_start[n_pass];
+    for (int e = 0; e < n_edges; ++e)
+      if (cap[e] < 1) fail(TN_ERR_INVALID, "cap entries must be >= 1");
+    ck(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // [cap (n_edges) | pass_start (n_pass + 1)]
+    std::vector<int32_t> h;
+    h.insert(h.end(), cap, cap + n_edges);
+    h.insert(h.end(), pass_start, pass_start + n_pass + 1);
+    int32_t* d = static_cast<int32_t*>(c->aux_buf.get(sizeof(int32_t) * h.size()));
+    ck(cudaMemcpyAsync(d, h.data(), sizeof(int32_t) * h.size(), cudaMemcpyHostToDevice, st),
+       "copy label tables");
+    ck(tn::launch_water_fill(spec_dev, d, d + n_edges, chi_uniform, n_pass, n_inst, chi_dev,
+                             feat_dev, st),
+       "water fill");
+    ck(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  });
+}
+
+extern "C" tn_status tn_rank_model_grad(tn_ctx_t* c, const float* X_dev, const float* y_dev,
+                                        const int32_t* idx_dev, int32_t n, const float* w_dev,
+                                        float* grad_dev, float* loss_dev, void* stream) {
+  if (!c) {
+    tn::set_error("tn_rank_model_grad: ctx is NULL");
+    return TN_ERR_INVALID;
+  }
+  return guarded(c, "tn_rank_model_grad", [&] {
+    if (!X_dev || !y_dev || !w_dev || !grad_dev || !loss_dev || n < 1)
+      fail(TN_ERR_INVALID, "invalid argument");
+    ck(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int np = tn::rank_model_params();
+    if (!idx_dev) {
+      int* iota = static_cast<int*>(c->aux_buf.get(sizeof(int) * size_t(n)));
+      ck(tn::launch_iota(iota, n, st), "iota");
+      idx_dev = iota;
+    }
+    ck(cudaMemsetAsync(grad_dev, 0, sizeof(float) * size_t(np), st), "memset grad");
+    ck(cudaMemsetAsync(loss_dev, 0, sizeof(float), st), "memset loss");
+    ck(tn::launch_mlp_grad(X_dev, y_dev, idx_dev, n, 1.f / float(n), w_dev, grad_dev, loss_dev,
+                           st),
+       "mlp grad");
+  });
+}
+
+extern "C" tn_status tn_rank_model_train(tn_ctx_t* c, const float* X_dev, const float* y_dev,
+                                         const int32_t* idx_dev, int32_t steps, int32_t batch,
+                                         float lr, float* w_dev, float* loss_dev, void* stream) {
+  if (!c) {
+    tn::set_error("tn_rank_model_train: ctx is NULL");
+    return TN_ERR_INVALID;
+  }
+  return guarded(c, "tn_rank_model_train", [&] {
+    if (!X_dev || !y_dev || !idx_dev || !w_dev || !loss_dev || steps < 1 || batch < 1 ||
+        !(lr > 0.f))
+      fail(TN_ERR_INVALID, "invalid argument");
+    ck(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int np = tn::rank_model_params();
+    float* g = static_cast<float*>(c->train_buf.get(3 * sizeof(float) * size_t(np)));
+    float* m = g + np;
+    float* v = m + np;
+    ck(cudaMemsetAsync(g, 0, 3 * sizeof(float) * size_t(np), st), "memset adam");
+    ck(cudaMemsetAsync(loss_dev, 0, sizeof(float) * size_t(steps), st), "memset loss");
+    for (int t = 0; t < steps; ++t) {
+      ck(tn::launch_mlp_grad(X_dev, y_dev, idx_dev + (long long)t * batch, batch,
+                             1.f / float(batch), w_dev, g, loss_dev + t, st),
+         "mlp grad");
+      ck(tn::launch_adam(w_dev, g, m, v, np, lr, 0.9f, 0.999f, 1e-8f, t + 1, st), "adam");
     }
   });
 }

@@ -97,6 +97,37 @@ cudaError_t launch_root_f32(const float* P, long long sP, int ldp, const float* 
 cudaError_t launch_close_f32(const float* Y, long long sY, const int64_t* y_off, const int32_t* D,
                              int n, int maxD, const double* logscale, double* logz, int* status,
                              int batch, cudaStream_t st);
+// ---- learned per-edge rank allocation (learned.cu)
+constexpr int kRankFeatures = 22;
+constexpr int kRankHidden = 64;
+struct RankArgs {
+  const double* lam; long long slam;  // descending eigenvalues of L_v, A of them per instance
+  int A, rk, dk;                      // dim A_v, structural rank of the chi_max plan, d_v
+  int v, nlegs, pass, npass;          // tree vertex, legs, DM pass index, DM passes
+  const void* model;                  // BF16 MLP parameters, or NULL: keep rk, record only
+  int budget_total, edges_after, first;  // per-pass budget; later vertices; first vertex
+  int chi_uniform;                    // rank of the uniform method the budget is taken from
+  int reserve_after;                  // budget kept for later vertices: sum min(2, r_u)
+  int* budget_rem;                    // per-instance running budget
+  int* prev_chi;                      // per-instance rank kept at the previous vertex
+  double* acc;                        // per-instance summed discarded share (or NULL)
+  int* rec_chi; float* rec_feat; double* rec_spec; long long rec_off;  // optional records
+};
+int rank_model_params();
+template <typename T>
+cudaError_t launch_rank_select(const RankArgs& g, T* U, long long sU, T* Ut, long long sUt,
+                               int batch, cudaStream_t st);
+cudaError_t launch_mlp_grad(const float* X, const float* tgt, const int* idx, int n, float scale,
+                            const float* w, float* grad, float* loss, cudaStream_t st);
+cudaError_t launch_adam(float* w, float* grad, float* m, float* v, int np, float lr, float b1,
+                        float b2, float eps, int t, cudaStream_t st);
+cudaError_t launch_to_bf16(const float* w, void* out, int np, cudaStream_t st);
+cudaError_t launch_water_fill(const double* spec, const int* cap, const int* pass_start,
+                              int chi_u, int n_pass, int B, int* chi_out, float* feat,
+                              cudaStream_t st);
+int water_fill_max_edges();
+cudaError_t launch_iota(int* x, int n, cudaStream_t st);
+
 template <typename T>
 size_t eigh_smem_bytes(int n, int r, int nlam);
 template <typename T>
