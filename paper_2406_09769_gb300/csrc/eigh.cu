@@ -384,6 +384,123 @@ __device__ __forceinline__ T quad_sum(T v) {
   return v;
 }
 
+// FP32 Householder tridiagonalisation with the matrix in registers: thread
+// (row ri = tid & 127, column half h = tid >> 7) holds A[ri][64 h .. 64 h + 63]
+// (zero outside n x n).  Step k: the owners of row k publish it (= column k)
+// to X; every warp forms the reflector from it (same arithmetic, same values)
+// and threads c < 128 write v_c to V (zero outside k+1 .. n-1); the rows'
+// partial products p = A v go to P; threads c write w_c = tau p_c - (tau^2 /
+// 2)(v.p) v_c to W (zero outside); then every row updates in place, A -= v
+// w^T + w v^T.  Zeros outside the active block make the inner loops plain
+// FMAs on broadcast float4 loads.  The reflectors are stored in column k of
+// As below the diagonal (v_{k+1} = 1) for the back-transformation; dd, ee,
+// tau as the shared-memory version.  X, V, W (128 each) and P (2 x 128) are
+// 16-byte aligned.
+__device__ void tridiag_regs_f32(float* As, int ld, int n, float* dd, float* ee, float* tau,
+                                 float* X, float* V, float* W, float* P) {
+  __shared__ __align__(16) float S2[2], D8[8];  // published row's tail norm; warp partials
+  const int tid = threadIdx.x, ri = tid & 127, h = tid >> 7, lane = tid & 31, cb = h * 64;
+  float a[64];
+#pragma unroll
+  for (int q = 0; q < 64; ++q) a[q] = (ri < n && cb + q < n) ? As[ri * ld + cb + q] : 0.f;
+  // row ri = k is published with sum_{c >= k + 2} A[k][c]^2 over this half
+  auto publish = [&](int k) {
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int q = 0; q < 64; q += 4) {
+      *reinterpret_cast<float4*>(X + cb + q) = make_float4(a[q], a[q + 1], a[q + 2], a[q + 3]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (cb + q + u >= k + 2) {
+          if (u & 1) s1 = fmaf(a[q + u], a[q + u], s1);
+          else s0 = fmaf(a[q + u], a[q + u], s0);
+        }
+    }
+    S2[h] = s0 + s1;
+  };
+  if (ri == 0) publish(0);
+  for (int k = 0; k + 2 < n; ++k) {
+    __syncthreads();  // row k published; the previous step's reads of V, W are done
+    const float s = S2[0] + S2[1];
+    const float alpha = X[k + 1];
+    float tk, beta, sc;
+    if (s == 0.f) {
+      tk = 0.f; beta = alpha; sc = 0.f;
+    } else {
+      beta = -copysignf(sqrtf(alpha * alpha + s), alpha);
+      tk = (beta - alpha) / beta;
+      sc = 1.f / (alpha - beta);
+    }
+    if (tid < 128) {
+      const int c = tid;
+      const float vc = (c == k + 1) ? 1.f : ((c > k + 1 && c < n && tk != 0.f) ? X[c] * sc : 0.f);
+      V[c] = vc;
+      if (c > k && c < n) As[c * ld + k] = vc;
+      if (c == 0) {
+        dd[k] = X[k];
+        ee[k] = beta;
+        tau[k] = tk;
+      }
+    }
+    __syncthreads();  // V complete; X free
+    const bool rowlive = ri > k && ri < n;
+    if (tk != 0.f) {  // uniform across the block
+      if (rowlive) {
+        float p0 = 0.f, p1 = 0.f;
+#pragma unroll
+        for (int q = 0; q < 64; q += 4) {
+          if (cb + q + 3 <= k || cb + q >= n) continue;  // warp-uniform: group inactive
+          const float4 v4 = *reinterpret_cast<const float4*>(V + cb + q);
+          p0 = fmaf(a[q], v4.x, p0);
+          p1 = fmaf(a[q + 1], v4.y, p1);
+          p0 = fmaf(a[q + 2], v4.z, p0);
+          p1 = fmaf(a[q + 3], v4.w, p1);
+        }
+        P[h * 128 + ri] = p0 + p1;
+      }
+      // v . p folded per warp (rows outside k+1 .. n-1 have v = 0)
+      {
+        float t = rowlive ? V[ri] * (P[h * 128 + ri]) : 0.f;
+        t = warp_sum(t);
+        if (lane == 0) D8[tid >> 5] = t;
+      }
+      __syncthreads();  // partial products of every row
+      const float4 d0 = *reinterpret_cast<const float4*>(D8);
+      const float4 d1 = *reinterpret_cast<const float4*>(D8 + 4);
+      const float dsum = tk * (((d0.x + d0.y) + (d0.z + d0.w)) + ((d1.x + d1.y) + (d1.z + d1.w)));
+      const float K = -0.5f * tk * dsum;
+      if (tid < 128) {
+        const int c = tid;
+        W[c] = (c > k && c < n) ? fmaf(K, V[c], tk * (P[c] + P[128 + c])) : 0.f;
+      }
+      __syncthreads();  // W complete
+      if (rowlive) {
+        const float vi = V[ri], wi = W[ri];
+#pragma unroll
+        for (int q = 0; q < 64; q += 4) {
+          if (cb + q + 3 <= k || cb + q >= n) continue;  // warp-uniform: group inactive
+          const float4 v4 = *reinterpret_cast<const float4*>(V + cb + q);
+          const float4 w4 = *reinterpret_cast<const float4*>(W + cb + q);
+          a[q] -= fmaf(vi, w4.x, wi * v4.x);
+          a[q + 1] -= fmaf(vi, w4.y, wi * v4.y);
+          a[q + 2] -= fmaf(vi, w4.z, wi * v4.z);
+          a[q + 3] -= fmaf(vi, w4.w, wi * v4.w);
+        }
+      }
+    }
+    if (ri == k + 1) publish(k + 1);
+  }
+  // the last 2 x 2 block for the caller's tail
+  if (ri >= n - 2 && ri < n) {
+#pragma unroll
+    for (int q = 0; q < 64; ++q) {
+      const int c = cb + q;
+      if (c >= n - 2 && c < n && c <= ri) As[ri * ld + c] = a[q];
+    }
+  }
+  __syncthreads();
+}
+
 template <typename T>
 __device__ int sturm_count_fast(const T* dd, const T* e2, int n, T x, T pivmin) {
   T q = dd[0] - x;
@@ -407,18 +524,19 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
   __shared__ T scal[8];
   const int ld = n + 1;
   const int nl = (nlam > r) ? nlam : r;
-  T* A = reinterpret_cast<T*>(raw);  // n x ld
-  T* Zs = A + n * ld;                 // r vectors of length n (column-major)
-  T* dd = Zs + r * (n + 1);          // Zs columns are padded to n + 1
+  // the 128-entry vectors first (16-byte aligned), then A and Z
+  T* dd = reinterpret_cast<T*>(raw);
   T* ee = dd + kNmax;
   T* e2 = ee + kNmax;
   T* tau = e2 + kNmax;
-  T* vb = tau + kNmax;
+  T* vb = tau + kNmax;                // vb, wv: 2 x 128, published rows (FP32)
   T* wv = vb + kNmax;
   T* part = wv + kNmax;               // 2 x 128
   T* lam = part + 2 * kNmax;          // kNmax
-  T* shift = lam + kNmax;             // 64
-  T* pub = shift + 64;                // kNmax
+  T* pub = lam + kNmax;               // kNmax
+  T* shift = pub + kNmax;             // 64
+  T* A = shift + 64;                  // n x ld
+  T* Zs = A + n * ld;                 // r vectors of length n, padded to n + 1
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int b = blockIdx.x;
   const T* L = Lg + (long long)b * sL;
@@ -439,6 +557,12 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
   }
 
   // ---- 1. Householder tridiagonalisation
+  if constexpr (sizeof(T) == 4) {
+    tridiag_regs_f32(reinterpret_cast<float*>(A), ld, n, reinterpret_cast<float*>(dd),
+                     reinterpret_cast<float*>(ee), reinterpret_cast<float*>(tau),
+                     reinterpret_cast<float*>(vb), reinterpret_cast<float*>(wv),
+                     reinterpret_cast<float*>(pub), reinterpret_cast<float*>(part));
+  } else {
   const int ri = tid & 127, half = tid >> 7;
   for (int k = 0; k + 2 < n; ++k) {
     const int m = n - k - 1;
@@ -503,6 +627,7 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
       for (int c = c0; c < c1; ++c) row[c] -= vi * wv[c] + wi * vb[c];
     }
     __syncthreads();
+  }
   }
   if (tid == 0) {
     if (n >= 2) {
@@ -747,7 +872,7 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
 
 template <typename T>
 size_t eigh_fast_smem_bytes(int n, int r) {
-  // A, Z, then dd ee e2 tau vb wv (6), part (2), lam (1), shift (64), pub (1)
+  // dd ee e2 tau vb wv (6), part (2), lam (1), pub (1), shift (64), then A, Z
   return sizeof(T) * (size_t(n) * (n + 1) + size_t(r) * (n + 1) + 10 * kNmax + 64);
 }
 

@@ -44,8 +44,10 @@ __device__ __forceinline__ double block_max_d(double v, double* red) {
   return red[0];
 }
 
-// Y[a, hl, e, b, hr] = inv_norm * sum_p S[a, p, b] T[p, hl, hr, e]  (FP64 sum, FP32 store)
-// and, when Yt is set, Yt[(e * Dr + b * dhr + hr) * Dl + a * dhl + hl] = same value.
+// Y[a, hl, e, b, hr] = inv_norm * sum_p S[a, p, b] T[p, hl, hr, e]  (FP32 arithmetic: a
+// sum over the bond dimension p, rounded once to the FP32 storage precision; FP64 units
+// are a small fraction of FP32 ones on this part) and, when Yt is set,
+// Yt[(e * Dr + b * dhr + hr) * Dl + a * dhl + hl] = same value.
 __global__ void __launch_bounds__(256) k_fuse_f32(const FuseSite* __restrict__ sites,
                                                   const double* const* tens,
                                                   const double* __restrict__ inv_norm, int nv,
@@ -64,14 +66,14 @@ __global__ void __launch_bounds__(256) k_fuse_f32(const FuseSite* __restrict__ s
   const int hl = int(t % f.dhl); t /= f.dhl;
   const int aa = int(t);
   const double* T = tens[i] + f.t_off + hl * f.shl + hr * f.shr + e * f.se;
-  double acc = 0.0;
+  float acc = 0.f;
   if (trivial) {
-    acc = T[0];
+    acc = float(T[0]);
   } else {
     const float* Sk = S + (long long)i * sS + f.s_off + (long long)aa * f.dp * f.b + bb;
-    for (int p = 0; p < f.dp; ++p) acc = fma((double)Sk[(long long)p * f.b], T[p * f.sp], acc);
+    for (int p = 0; p < f.dp; ++p) acc = fmaf(Sk[(long long)p * f.b], float(T[p * f.sp]), acc);
   }
-  const float v = float(acc * inv_norm[(long long)i * nv + f.vertex]);
+  const float v = acc * float(inv_norm[(long long)i * nv + f.vertex]);
   Y[(long long)i * sY + f.y_off + o] = v;
   if (Yt) {
     const long long Dl = (long long)f.a * f.dhl, Dr = (long long)f.b * f.dhr;
@@ -99,7 +101,7 @@ __global__ void __launch_bounds__(256) k_fuse_f32_tiled(const FuseSite* __restri
   if (j0 >= J || a0 >= Dl) return;  // uniform per block
   const double* Tb = tens[i] + f.t_off;
   const float* Si = S + (long long)i * sS + f.s_off;
-  const double inv = inv_norm[(long long)i * nv + f.vertex];
+  const float inv = float(inv_norm[(long long)i * nv + f.vertex]);
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int j = j0 + tx;
   int e = 0, bb = 0, hr = 0;
@@ -117,9 +119,9 @@ __global__ void __launch_bounds__(256) k_fuse_f32_tiled(const FuseSite* __restri
       const int aa = ap / f.dhl, hl = ap - aa * f.dhl;
       const double* T = Tb + hl * f.shl + hr * f.shr + e * f.se;
       const float* Sk = Si + (long long)aa * f.dp * f.b + bb;
-      double acc = 0.0;
-      for (int p = 0; p < f.dp; ++p) acc = fma((double)Sk[(long long)p * f.b], T[p * f.sp], acc);
-      v = float(acc * inv);
+      float acc = 0.f;
+      for (int p = 0; p < f.dp; ++p) acc = fmaf(Sk[(long long)p * f.b], float(T[p * f.sp]), acc);
+      v = acc * inv;
       Y[(long long)i * sY + f.y_off + (long long)ap * J + j] = v;
     }
     tile[ty + 8 * q][tx] = v;
