@@ -393,11 +393,16 @@ __device__ __forceinline__ T quad_sum(T v) {
 // 2)(v.p) v_c to W (zero outside); then every row updates in place, A -= v
 // w^T + w v^T.  Zeros outside the active block make the inner loops plain
 // FMAs on broadcast float4 loads.  The reflectors are stored in column k of
-// As below the diagonal (v_{k+1} = 1) for the back-transformation; dd, ee,
-// tau as the shared-memory version.  X, V, W (128 each) and P (2 x 128) are
-// 16-byte aligned.
-__device__ void tridiag_regs_f32(float* As, int ld, int n, float* dd, float* ee, float* tau,
-                                 float* X, float* V, float* W, float* P) {
+// R as rows: R[k * kRld + c + (c / 32) * 4] = v_c for c < 128 (zero outside
+// k+1 .. n-1, v_{k+1} = 1; the padding puts the four 32-row quarters in
+// disjoint bank groups); R may overlay As, which is read only at the start.
+// dd, ee, tau as the shared-memory version.  X, V, W (128 each) and P
+// (2 x 128) are 16-byte aligned.
+constexpr int kRld = 144;
+__device__ __forceinline__ int rpad(int c) { return c + (c >> 5) * 4; }
+
+__device__ void tridiag_regs_f32(const float* As, int ld, int n, float* R, float* dd, float* ee,
+                                 float* tau, float* X, float* V, float* W, float* P) {
   __shared__ __align__(16) float S2[2], D8[8];  // published row's tail norm; warp partials
   const int tid = threadIdx.x, ri = tid & 127, h = tid >> 7, lane = tid & 31, cb = h * 64;
   float a[64];
@@ -435,7 +440,7 @@ __device__ void tridiag_regs_f32(float* As, int ld, int n, float* dd, float* ee,
       const int c = tid;
       const float vc = (c == k + 1) ? 1.f : ((c > k + 1 && c < n && tk != 0.f) ? X[c] * sc : 0.f);
       V[c] = vc;
-      if (c > k && c < n) As[c * ld + k] = vc;
+      R[k * kRld + rpad(c)] = vc;
       if (c == 0) {
         dd[k] = X[k];
         ee[k] = beta;
@@ -490,13 +495,18 @@ __device__ void tridiag_regs_f32(float* As, int ld, int n, float* dd, float* ee,
     }
     if (ri == k + 1) publish(k + 1);
   }
-  // the last 2 x 2 block for the caller's tail
+  // the last 2 x 2 block of T
   if (ri >= n - 2 && ri < n) {
 #pragma unroll
     for (int q = 0; q < 64; ++q) {
       const int c = cb + q;
-      if (c >= n - 2 && c < n && c <= ri) As[ri * ld + c] = a[q];
+      if (c == ri) dd[ri] = a[q];
+      if (c == ri - 1 && ri == n - 1) ee[n - 2] = a[q];
     }
+  }
+  if (tid == 0) {
+    ee[n - 1] = 0.f;
+    if (n >= 2) tau[n - 2] = 0.f;
   }
   __syncthreads();
 }
@@ -512,6 +522,113 @@ __device__ int sturm_count_fast(const T* dd, const T* e2, int n, T x, T pivmin) 
     c += (q < T(0));
   }
   return c;
+}
+
+// FP32 phases 4-6: thread quad (column col = tid / 4, quarter qr = tid % 4)
+// holds rows qr * 32 .. qr * 32 + 31 of its vector (z[kk] = row qr * 32 + kk),
+// so the quad's reads of a shared vector are float4 loads at padded offsets
+// qr * 36 + kk (disjoint bank groups, broadcast across quads).  Modified
+// Gram-Schmidt in descending eigenvalue order with double-buffered published
+// vectors (one barrier per vector), then U = H_0 ... H_{n-3} Z from the
+// padded reflector rows R, then signs (largest-|.| entry, first on ties,
+// positive) and the stores U (n x r) and Ut (r x n).
+__device__ void vectors_f32(const float* Zs, int zld, int n, int r, const float* R,
+                            const float* tau, float* pub, float* U, float* Ut) {
+  const int tid = threadIdx.x, col = tid >> 2, qr = tid & 3;
+  const bool live = col < r;
+  float z[kQ];
+#pragma unroll
+  for (int kk = 0; kk < kQ; ++kk) {
+    const int row = qr * kQ + kk;
+    z[kk] = (live && row < n) ? Zs[col * zld + row] : 0.f;
+  }
+  auto load = [&](const float* src, float* v) {
+#pragma unroll
+    for (int m = 0; m < kQ / 4; ++m) {
+      const float4 t = *reinterpret_cast<const float4*>(src + qr * 36 + 4 * m);
+      v[4 * m] = t.x; v[4 * m + 1] = t.y; v[4 * m + 2] = t.z; v[4 * m + 3] = t.w;
+    }
+  };
+  auto normalise_publish = [&](float* dst) {
+    float s = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < kQ; ++kk) s = fmaf(z[kk], z[kk], s);
+    s = quad_sum(s);
+    const float inv = (s > 0.f) ? 1.f / sqrtf(s) : 0.f;
+#pragma unroll
+    for (int kk = 0; kk < kQ; ++kk) z[kk] *= inv;
+#pragma unroll
+    for (int m = 0; m < kQ / 4; ++m)
+      *reinterpret_cast<float4*>(dst + qr * 36 + 4 * m) =
+          make_float4(z[4 * m], z[4 * m + 1], z[4 * m + 2], z[4 * m + 3]);
+  };
+  if (col == 0) normalise_publish(pub);
+  for (int j = 0; j < r; ++j) {
+    __syncthreads();  // vector j published; the reads of the other buffer are done
+    if (live && col > j) {
+      float p[kQ];
+      load(pub + (j & 1) * kRld, p);
+      float d = 0.f;
+#pragma unroll
+      for (int kk = 0; kk < kQ; ++kk) d = fmaf(p[kk], z[kk], d);
+      d = quad_sum(d);
+#pragma unroll
+      for (int kk = 0; kk < kQ; ++kk) z[kk] = fmaf(-d, p[kk], z[kk]);
+      if (col == j + 1) normalise_publish(pub + ((j + 1) & 1) * kRld);
+    }
+  }
+  if (live) {
+    for (int k = n - 3; k >= 0; --k) {
+      const float tk = tau[k];
+      if (tk == 0.f) continue;
+      float v[kQ];
+      load(R + k * kRld, v);
+      float d = 0.f;
+#pragma unroll
+      for (int kk = 0; kk < kQ; ++kk) d = fmaf(v[kk], z[kk], d);
+      d = quad_sum(d) * tk;
+#pragma unroll
+      for (int kk = 0; kk < kQ; ++kk) z[kk] = fmaf(-d, v[kk], z[kk]);
+    }
+    float best = -1.f;
+    int bi = kNmax;
+#pragma unroll
+    for (int kk = 0; kk < kQ; ++kk) {
+      const int row = qr * kQ + kk;
+      const float a = fabsf(z[kk]);
+      if (row < n && (a > best || (a == best && row < bi))) { best = a; bi = row; }
+    }
+    const unsigned qm = 0xFu << (threadIdx.x & 28);
+    for (int o = 1; o <= 2; o <<= 1) {
+      const float ob = __shfl_xor_sync(qm, best, o);
+      const int oi = __shfl_xor_sync(qm, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    float sv = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < kQ; ++kk)
+      if (qr * kQ + kk == bi) sv = z[kk];
+    sv = quad_sum(sv);
+    const float sgn = (sv < 0.f) ? -1.f : 1.f;
+#pragma unroll
+    for (int kk = 0; kk < kQ; ++kk) {
+      const int row = qr * kQ + kk;
+      if (row < n) {
+        U[(long long)row * r + col] = sgn * z[kk];
+        if (Ut) Ut[(long long)col * n + row] = sgn * z[kk];
+      }
+    }
+  }
+}
+
+// Elements of the A region: the n x (n + 1) matrix, or for FP32 the larger of
+// that and the padded reflector rows (n - 2) x kRld.
+template <typename T>
+__host__ __device__ __forceinline__ int fast_region_a(int n) {
+  const int m = n * (n + 1);
+  if (sizeof(T) == 8) return m;
+  const int rr = (n > 2 ? n - 2 : 0) * kRld;
+  return m > rr ? m : rr;
 }
 
 template <typename T>
@@ -533,10 +650,10 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
   T* wv = vb + kNmax;
   T* part = wv + kNmax;               // 2 x 128
   T* lam = part + 2 * kNmax;          // kNmax
-  T* pub = lam + kNmax;               // kNmax
-  T* shift = pub + kNmax;             // 64
-  T* A = shift + 64;                  // n x ld
-  T* Zs = A + n * ld;                 // r vectors of length n, padded to n + 1
+  T* pub = lam + kNmax;               // 3 x kNmax (FP32: two padded vectors of 144)
+  T* shift = pub + 3 * kNmax;         // 64
+  T* A = shift + 64;                  // n x ld; FP32: reflector rows R overlay it
+  T* Zs = A + fast_region_a<T>(n);    // r vectors of length n, padded to n + 1
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int b = blockIdx.x;
   const T* L = Lg + (long long)b * sL;
@@ -558,7 +675,8 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
 
   // ---- 1. Householder tridiagonalisation
   if constexpr (sizeof(T) == 4) {
-    tridiag_regs_f32(reinterpret_cast<float*>(A), ld, n, reinterpret_cast<float*>(dd),
+    tridiag_regs_f32(reinterpret_cast<float*>(A), ld, n, reinterpret_cast<float*>(A),
+                     reinterpret_cast<float*>(dd),
                      reinterpret_cast<float*>(ee), reinterpret_cast<float*>(tau),
                      reinterpret_cast<float*>(vb), reinterpret_cast<float*>(wv),
                      reinterpret_cast<float*>(pub), reinterpret_cast<float*>(part));
@@ -630,13 +748,15 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
   }
   }
   if (tid == 0) {
-    if (n >= 2) {
-      dd[n - 2] = A[(n - 2) * ld + (n - 2)];
-      ee[n - 2] = A[(n - 1) * ld + (n - 2)];
-      tau[n - 2] = T(0);
+    if constexpr (sizeof(T) == 8) {  // the FP32 version wrote them from registers
+      if (n >= 2) {
+        dd[n - 2] = A[(n - 2) * ld + (n - 2)];
+        ee[n - 2] = A[(n - 1) * ld + (n - 2)];
+        tau[n - 2] = T(0);
+      }
+      dd[n - 1] = A[(n - 1) * ld + (n - 1)];
+      ee[n - 1] = T(0);
     }
-    dd[n - 1] = A[(n - 1) * ld + (n - 1)];
-    ee[n - 1] = T(0);
     T gl = dd[0], gu = dd[0], emax = T(0);
     for (int j = 0; j < n; ++j) {
       const T el = (j > 0) ? fabs(ee[j - 1]) : T(0);
@@ -772,6 +892,12 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
   }
   __syncthreads();
 
+  if constexpr (sizeof(T) == 4) {
+    vectors_f32(reinterpret_cast<const float*>(Zs), zld, n, r,
+                reinterpret_cast<const float*>(A), reinterpret_cast<const float*>(tau),
+                reinterpret_cast<float*>(pub), reinterpret_cast<float*>(Ug) + (long long)b * sU,
+                Utg ? reinterpret_cast<float*>(Utg) + (long long)b * sUt : nullptr);
+  } else {
   // ---- 4. vectors into registers: thread = (column c, quarter q of the rows)
   const int col = tid >> 2, qr = tid & 3;
   const bool live = col < r;
@@ -864,6 +990,7 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
       }
     }
   }
+  }
   if (lamg) {
     double* lo = lamg + (long long)b * slam;
     for (int t = tid; t < nlam && t < n; t += kThreads) lo[t] = double(lam[t]);
@@ -872,8 +999,8 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
 
 template <typename T>
 size_t eigh_fast_smem_bytes(int n, int r) {
-  // dd ee e2 tau vb wv (6), part (2), lam (1), pub (1), shift (64), then A, Z
-  return sizeof(T) * (size_t(n) * (n + 1) + size_t(r) * (n + 1) + 10 * kNmax + 64);
+  // dd ee e2 tau vb wv (6), part (2), lam (1), pub (3), shift (64), then A, Z
+  return sizeof(T) * (size_t(fast_region_a<T>(n)) + size_t(r) * (n + 1) + 12 * kNmax + 64);
 }
 
 }  // namespace
