@@ -6,19 +6,22 @@
 // X_i = X + i * sX.  Every density-matrix contraction of the method is cast in
 // this form (B = R is symmetric; transposed copies are written where needed).
 //
-// One CTA of 128 threads computes a 128 x BN tile (BN <= 256, multiple of 16):
+// One CTA of 256 threads computes a 128 x BN tile (BN <= 256, multiple of 16):
 //   * thread 0 streams 32-wide K chunks of A and B into 128B-swizzled shared
 //     memory with 3D TMA loads (batch = third dimension; out-of-range rows,
-//     columns and K are zero-filled by TMA), through a ring of stages guarded
-//     by mbarriers;
+//     columns and K are zero-filled by TMA), through a ring of up to four
+//     stages guarded by mbarriers (all chunks of a K = 128 contraction in
+//     flight at once);
 //   * thread 0 issues tcgen05.mma.cta_group::1.kind::tf32 (M = 128, N = BN,
 //     K = 8 per instruction), accumulating in TMEM (128 lanes x BN columns),
 //     and tcgen05.commit releases each stage;
-//   * with `split`, every staged tile is split in place into x = hi + lo
-//     (hi = x rounded to TF32) and three products hi*hi + hi*lo + lo*hi are
-//     accumulated: the compensated pass of the value path (~FP32 accuracy);
-//   * the four warps read their 32 TMEM lanes with tcgen05.ld.32x32b, scale,
-//     and store C (row-major) and/or C^T, folding max|C| into an atomic slot.
+//   * with `split`, every staged tile is split into x = hi + lo (hi = x
+//     rounded to TF32, in place; lo into one of two buffers of its own) and
+//     three products hi*hi + hi*lo + lo*hi are accumulated: the compensated
+//     pass of the value path (~FP32 accuracy);
+//   * the eight warps read TMEM (warp w: lanes 32 (w % 4) .., alternate
+//     16-column groups) with tcgen05.ld.32x32b, scale, and store C (row-major)
+//     and/or C^T, folding max|C| into an atomic slot.
 // Every mbarrier wait is bounded; on expiry the kernel sets *err, waits
 // (bounded) for its own TMA copies, frees its TMEM and returns.
 #include <cuda.h>
@@ -33,7 +36,9 @@ namespace tn {
 
 namespace {
 
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 256;
+constexpr int kLoBufs = 1;                    // lo halves of split chunks in flight
+constexpr uint32_t kEpiBytes = 8 * 32 * 33 * 4;  // per-warp 32 x 32 transpose tiles (padded)
 constexpr int kChunk = 32;                    // K elements per stage (128 bytes of FP32)
 constexpr uint32_t kWaitLimit = 1u << 22;     // bounded spin on every mbarrier
 
@@ -147,10 +152,14 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(const __grid_constant__ 
   const uint32_t a_bytes = 128 * 128;
   const uint32_t b_bytes = uint32_t(BN) * 128;
   const uint32_t tile_bytes = a_bytes + b_bytes;
-  const uint32_t stage_bytes = g.split ? 2 * tile_bytes : tile_bytes;
-  uint64_t* full = reinterpret_cast<uint64_t*>(base + stages * stage_bytes);
+  const int nlo = g.split ? kLoBufs : 0;
+  unsigned char* lo_base = base + stages * tile_bytes;
+  uint32_t region = (stages + nlo) * tile_bytes;  // the epilogue reuses it for transposes
+  if (region < kEpiBytes) region = kEpiBytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + region);
   uint64_t* freed = full + stages;
-  uint64_t* done = freed + stages;
+  uint64_t* lofree = freed + stages;   // kLoBufs
+  uint64_t* done = lofree + kLoBufs;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
 
@@ -170,6 +179,7 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(const __grid_constant__ 
       mbar_init(&full[s], 1);
       mbar_init(&freed[s], 1);
     }
+    for (int q = 0; q < kLoBufs; ++q) mbar_init(&lofree[q], 1);
     mbar_init(done, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -180,11 +190,17 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(const __grid_constant__ 
   const uint32_t tmem = *tmem_slot;
   const uint32_t idesc = idesc_tf32(128, BN);
 
+  // Every chunk's TMA is issued as early as its stage allows: all of them up
+  // front when the ring holds the whole K extent; otherwise the stage of chunk
+  // kc - 1 is refilled right after chunk kc's MMAs are issued (its own MMAs,
+  // issued one chunk earlier, have usually completed by then).  With `split`
+  // the lo halves go to kLoBufs buffers of their own, so a stage is released
+  // by the MMAs alone and loads overlap the split of later chunks.
   int issued = 0;    // chunks whose TMA has been issued (thread 0)
   int consumed = 0;  // chunks whose arrival thread 0 has observed
   auto issue = [&](int kc) {
     const int s = kc % stages;
-    unsigned char* st = base + s * stage_bytes;
+    unsigned char* st = base + s * tile_bytes;
     mbar_expect_tx(&full[s], tile_bytes);
     tma_load_3d(st, &tmA, &full[s], kc * kChunk, m0, bi);
     tma_load_3d(st + a_bytes, &tmB, &full[s], kc * kChunk, n0, bi);
@@ -192,72 +208,76 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(const __grid_constant__ 
   if (tid == 0) {
     for (; issued < nk && issued < stages; ++issued) issue(issued);
   }
-  bool ok = true;
+  int mma_chunks = 0;  // chunks whose MMAs thread 0 has issued
   for (int kc = 0; kc < nk; ++kc) {
     const int s = kc % stages;
     const uint32_t ph = uint32_t(kc / stages) & 1u;
-    unsigned char* st = base + s * stage_bytes;
+    unsigned char* st = base + s * tile_bytes;
+    unsigned char* lo = lo_base + (kc % kLoBufs) * tile_bytes;
     if (g.split) {
-      // every thread waits for the chunk, then splits it in place (hi) and
-      // into the lo copy; the async proxy sees the writes after the fence.
-      const bool arrived = mbar_wait(&full[s], ph);
-      if (!arrived) atomicExch(abort_flag, 1);
-      if (tid == 0 && arrived) consumed = kc + 1;
+      // every thread: the chunk has landed and its lo buffer is free (the
+      // MMAs of chunk kc - kLoBufs have completed); then split in place
+      bool ok = mbar_wait(&full[s], ph);
+      if (ok && kc >= kLoBufs)
+        ok = mbar_wait(&lofree[kc % kLoBufs], uint32_t(kc / kLoBufs - 1) & 1u);
+      if (!ok) atomicExch(abort_flag, 1);
+      if (tid == 0 && ok) consumed = kc + 1;
       __syncthreads();
-      if (*abort_flag) { ok = false; break; }
+      if (*abort_flag) break;
       float4* hi = reinterpret_cast<float4*>(st);
-      float4* lo = reinterpret_cast<float4*>(st + tile_bytes);
+      float4* lq = reinterpret_cast<float4*>(lo);
       for (uint32_t q = tid; q < tile_bytes / 16; q += kTcThreads) {
-        float4 x = hi[q];
-        float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+        const float4 x = hi[q];
+        const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
         hi[q] = h;
-        lo[q] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+        lq[q] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
     }
     if (tid == 0) {
+      bool ok = true;
       if (!g.split) {
-        if (mbar_wait(&full[s], ph)) {
-          consumed = kc + 1;
-        } else {
-          *abort_flag = 1;
-          ok = false;
-        }
+        ok = mbar_wait(&full[s], ph);
+        if (ok) consumed = kc + 1;
+        else *abort_flag = 1;
       }
       if (ok) {
         tc_fence_after();
         const uint32_t a0 = su32(st), b0 = su32(st + a_bytes);
+        const uint32_t al0 = su32(lo), bl0 = su32(lo + a_bytes);
         for (int j = 0; j < kChunk / 8; ++j) {
           const uint32_t acc = (kc > 0 || j > 0) ? 1u : 0u;
           const uint64_t ah = desc_sw128(a0 + 32 * j), bh = desc_sw128(b0 + 32 * j);
           umma_tf32(tmem, ah, bh, idesc, acc);
           if (g.split) {
-            const uint64_t al = desc_sw128(a0 + tile_bytes + 32 * j);
-            const uint64_t bl = desc_sw128(b0 + tile_bytes + 32 * j);
-            umma_tf32(tmem, ah, bl, idesc, 1u);
-            umma_tf32(tmem, al, bh, idesc, 1u);
+            umma_tf32(tmem, ah, desc_sw128(bl0 + 32 * j), idesc, 1u);
+            umma_tf32(tmem, desc_sw128(al0 + 32 * j), bh, idesc, 1u);
           }
         }
         umma_commit(&freed[s]);
-        if (issued < nk) {
-          // the stage is reloaded once the MMAs reading it have completed
-          if (!mbar_wait(&freed[s], ph)) {
-            *abort_flag = 1;
-            ok = false;
-          } else {
+        if (g.split) umma_commit(&lofree[kc % kLoBufs]);
+        mma_chunks = kc + 1;
+        // refill the stage of chunk kc - 1 (of chunk kc itself with a single
+        // stage) with the next chunk
+        const int pc = (stages > 1) ? kc - 1 : kc;
+        if (pc >= 0 && issued < nk) {
+          if (mbar_wait(&freed[pc % stages], uint32_t(pc / stages) & 1u)) {
             issue(issued);
             ++issued;
+          } else {
+            *abort_flag = 1;
           }
         }
       }
     }
-    if (!ok) break;
+    if (!g.split && tid == 0 && *abort_flag) break;  // thread 0 alone runs the non-split loop
   }
-  if (tid == 0 && ok) umma_commit(done);
+  // every MMA issued so far has completed before TMEM is read or released
+  if (tid == 0) umma_commit(done);
   __syncthreads();
-  bool good = (*abort_flag == 0);
-  if (good && !mbar_wait(done, 0)) good = false;
+  bool good = (*abort_flag == 0) && (mma_chunks == nk || tid != 0);
+  if (!mbar_wait(done, 0)) good = false;
   if (!__syncthreads_and(good)) {
     good = false;
     if (tid == 0) {
@@ -275,20 +295,26 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(const __grid_constant__ 
       const float mx = __uint_as_float(g.amax_in[(long long)bi * g.s_amax_in]);
       alpha = (mx > 0.f) ? 1.f / mx : 1.f;
     }
-    const int row = warp * 32 + lane;
-    const int gm = m0 + row;
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31 (one row each) and every other
+    // 32-column group; C^T is stored from there (lanes = rows run along C^T's
+    // rows), C after a transpose through a per-warp shared tile (lanes =
+    // columns, 128-byte rows).  TMEM holds at least round_up(BN, 32) columns.
+    const int rbase = m0 + (warp & 3) * 32;
+    const int gm = rbase + lane;
+    float* tile = reinterpret_cast<float*>(base) + warp * (32 * 33);
     float lmax = 0.f;
     bool bad = false;
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-      uint32_t v[16];
-      tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(c0), v);
-      if (gm < g.M) {
+    for (int c0 = 32 * (warp >> 2); c0 < BN; c0 += 64) {
+      uint32_t v[32];
+      const uint32_t taddr = tmem + (uint32_t((warp & 3) * 32) << 16) + uint32_t(c0);
+      tmem_ld16(taddr, *reinterpret_cast<uint32_t(*)[16]>(&v[0]));
+      tmem_ld16(taddr + 16, *reinterpret_cast<uint32_t(*)[16]>(&v[16]));
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int gn = n0 + c0 + j;
-          if (gn >= g.N) break;
-          const float x = alpha * __uint_as_float(v[j]);
-          if (g.C) g.C[(long long)bi * g.sC + (long long)gm * g.ldc + gn] = x;
+      for (int j = 0; j < 32; ++j) {
+        const int gn = n0 + c0 + j;
+        const float x = alpha * __uint_as_float(v[j]);
+        tile[lane * 33 + j] = x;
+        if (gm < g.M && gn < g.N) {
           if (g.Ct) {
             const int q = gn / g.ct_cols, cc = gn - q * g.ct_cols;
             g.Ct[(long long)bi * g.sCt + (long long)cc * g.ldct + (long long)gm * (g.N / g.ct_cols) + q] = x;
@@ -297,6 +323,16 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(const __grid_constant__ 
           bad |= !isfinite(x);
         }
       }
+      __syncwarp();
+      if (g.C) {
+        const int gn = n0 + c0 + lane;
+        if (gn < g.N) {
+          float* Cb = g.C + (long long)bi * g.sC + gn;
+          for (int i = 0; i < 32 && rbase + i < g.M; ++i)
+            Cb[(long long)(rbase + i) * g.ldc] = tile[i * 33 + lane];
+        }
+      }
+      __syncwarp();
     }
     if (g.amax_out) {
       if (bad) lmax = INFINITY;
@@ -350,18 +386,23 @@ bool make_map(CUtensorMap* m, const float* ptr, int K, int rows, int batch, long
 }  // namespace
 
 size_t tc_gemm_smem_bytes(int BN, int split, int K, int* stages_out) {
-  // Stages are sized so that at least two CTAs share an SM (the per-instance
-  // tiles are small and latency-bound: co-resident CTAs hide each other's
-  // load and epilogue latency), and never exceed the number of K chunks.
+  // A ring of K-chunk stages (TMA targets), up to 4 and no more than the K
+  // chunks, plus kLoBufs buffers for the lo halves of split chunks, within
+  // ~104 KB so that two CTAs share an SM (measured best for the per-instance
+  // 128 x 128 x 128..256 contractions: one CTA's loads and epilogue overlap
+  // the other's MMAs).
   const size_t tile = size_t(128 + BN) * 128;
-  const size_t stage = split ? 2 * tile : tile;
-  int stages = int((108 * 1024) / stage);
+  const size_t lo = split ? kLoBufs * tile : 0;
+  const size_t budget = 104 * 1024;
+  int stages = budget > lo ? int((budget - lo) / tile) : 1;
   const int nk = (K + kChunk - 1) / kChunk;
   if (stages > nk) stages = nk;
   if (stages > 4) stages = 4;
   if (stages < 1) stages = 1;
   if (stages_out) *stages_out = stages;
-  return 1024 + stages * stage + (2 * stages + 1) * 8 + 16;
+  size_t region = stages * tile + lo;
+  if (region < kEpiBytes) region = kEpiBytes;
+  return 1024 + region + (2 * stages + kLoBufs + 1) * 8 + 16;
 }
 
 cudaError_t tc_gemm_configure() {
