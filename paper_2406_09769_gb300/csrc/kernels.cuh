@@ -84,7 +84,7 @@ cudaError_t launch_eigh_top(const T* L, long long sL, T* U, long long sU, T* Ut,
 
 // FP32-storage kernels of the mixed-precision path (see kernels_f32.cu).
 cudaError_t launch_fuse_f32(const FuseSite* sites, int n, int max_elems, int max_dl, int max_j,
-                            const double* const* tens,
+                            int max_t, const double* const* tens,
                             const double* inv_norm, int nv, const float* S, long long sS,
                             int trivial, float* Y, long long sY, float* Yt, const int64_t* yt_off,
                             int batch, cudaStream_t st);

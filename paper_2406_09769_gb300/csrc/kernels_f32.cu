@@ -135,6 +135,85 @@ __global__ void __launch_bounds__(256) k_fuse_f32_tiled(const FuseSite* __restri
   }
 }
 
+// Wider tile of the same fusion: block of 256 threads owns 32 rows a' x 128
+// columns j; thread (c, g) = (tid % 32, tid / 32) computes j = j0 + c + 32 u and
+// a' = a0 + g + 8 q (u, q = 0..3), so every Y store instruction writes 32
+// consecutive j of one row, and Yt is written from a [32][129] shared tile
+// (odd stride: conflict-free column reads) along a'.  The site tensor's
+// (at most kFuseT) entries are staged as FP32 in shared memory.
+constexpr int kFuseT = 256;
+__global__ void __launch_bounds__(256) k_fuse_f32_wide(const FuseSite* __restrict__ sites,
+                                                       int n_sites, const double* const* tens,
+                                                       const double* __restrict__ inv_norm,
+                                                       int nv, const float* __restrict__ S,
+                                                       long long sS, float* __restrict__ Y,
+                                                       long long sY, float* __restrict__ Yt,
+                                                       const int64_t* yt_off) {
+  __shared__ float tile[32][129];
+  __shared__ float ts[kFuseT];
+  const int site = blockIdx.z % n_sites, i = blockIdx.z / n_sites;
+  const FuseSite f = sites[site];
+  const int Dl = f.a * f.dhl, Dr = f.b * f.dhr, J = f.de * Dr;
+  const int j0 = blockIdx.x * 128, a0 = blockIdx.y * 32;
+  if (j0 >= J || a0 >= Dl) return;  // uniform per block
+  const int tid = threadIdx.x, c = tid & 31, g = tid >> 5;
+  // T[p][hl][hr][e] (strides sp, shl, shr, se) staged densely as [p][hl][hr][e]
+  const int nT = f.dp * f.dhl * f.dhr * f.de;
+  const double* Tb = tens[i] + f.t_off;
+  for (int q = tid; q < nT; q += 256) {
+    int t = q;
+    const int e = t % f.de; t /= f.de;
+    const int hr = t % f.dhr; t /= f.dhr;
+    const int hl = t % f.dhl; t /= f.dhl;
+    ts[q] = float(Tb[t * f.sp + hl * f.shl + hr * f.shr + e * f.se]);
+  }
+  __syncthreads();
+  const float* Si = S + (long long)i * sS + f.s_off;
+  const float inv = float(inv_norm[(long long)i * nv + f.vertex]);
+  const int tp = f.dhl * f.dhr * f.de;  // stride of p in ts
+  int jb[4], jt[4];                     // per column: S offset (b), ts offset (hr, e)
+  bool jok[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int j = j0 + c + 32 * u;
+    jok[u] = j < J;
+    const int e = jok[u] ? j / Dr : 0;
+    const int cc = jok[u] ? j - e * Dr : 0;
+    const int bb = cc / f.dhr, hr = cc - bb * f.dhr;
+    jb[u] = bb;
+    jt[u] = hr * f.de + e;
+  }
+  float* Yi = Y + (long long)i * sY + f.y_off;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int ap = a0 + g + 8 * q;
+    const bool aok = ap < Dl;
+    const int aa = aok ? ap / f.dhl : 0, hl = aok ? ap - aa * f.dhl : 0;
+    const float* Sk = Si + (long long)aa * f.dp * f.b;
+    const int tb = hl * f.dhr * f.de;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      float v = 0.f;
+      if (aok && jok[u]) {
+        float acc = 0.f;
+        for (int p = 0; p < f.dp; ++p)
+          acc = fmaf(Sk[(long long)p * f.b + jb[u]], ts[p * tp + tb + jt[u]], acc);
+        v = acc * inv;
+        Yi[(long long)ap * J + j0 + c + 32 * u] = v;
+      }
+      tile[g + 8 * q][c + 32 * u] = v;
+    }
+  }
+  if (!Yt) return;  // uniform
+  __syncthreads();
+  float* Yti = Yt + (long long)i * sY + yt_off[site];
+  const int ap = a0 + c;
+  for (int jj = g; jj < 128; jj += 8) {
+    const int j = j0 + jj;
+    if (j < J && ap < Dl) Yti[(long long)j * Dl + ap] = tile[c][jj];
+  }
+}
+
 __global__ void k_fill_env_root_f32(float* R, long long sR, unsigned int* amax, long long s_amax,
                                     int batch) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -263,11 +342,17 @@ cudaError_t launch_sgemm_nt(const TcGemmArgs& g, cudaStream_t st) {
 }
 
 cudaError_t launch_fuse_f32(const FuseSite* sites, int n, int max_elems, int max_dl, int max_j,
-                            const double* const* tens,
+                            int max_t, const double* const* tens,
                             const double* inv_norm, int nv, const float* S, long long sS,
                             int trivial, float* Y, long long sY, float* Yt, const int64_t* yt_off,
                             int batch, cudaStream_t st) {
   if (Yt && !trivial && max_dl > 0 && max_j > 0) {
+    if (max_t <= kFuseT) {
+      dim3 grid((max_j + 127) / 128, (max_dl + 31) / 32, n * batch);
+      k_fuse_f32_wide<<<grid, 256, 0, st>>>(sites, n, tens, inv_norm, nv, S, sS, Y, sY, Yt,
+                                            yt_off);
+      return cudaGetLastError();
+    }
     dim3 grid((max_j + 31) / 32, (max_dl + 31) / 32, n * batch);
     k_fuse_f32_tiled<<<grid, dim3(32, 8), 0, st>>>(sites, n, tens, inv_norm, nv, S, sS, Y, sY, Yt,
                                                    yt_off);
