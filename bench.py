@@ -16,6 +16,7 @@ a 256 MB buffer is rewritten between steps (L2 flush, outside the events);
 barrier + synchronize on both sides; the max over ranks is reported.
 """
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -330,14 +331,18 @@ def bench_ours(args):
         is_tf32 = prec in (B.TN_PREC_TF32, B.TN_PREC_TF32_FAST)
         peak = bf16 * (TF32_PER_BF16 if is_tf32 else 1.0)
         bound, note = "tensor", f"{pk_src} bf16 sustained" + (" x 1.1/2.25 (tf32)" if is_tf32 else "")
+    # DRAM bytes per launch of the dominant kernel from an ncu capture; null when
+    # the kernel's source has changed since the counters were taken
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
         with open(tpath) as f:
             tr = json.load(f)
-        key = f"{args.precision}:{dom}"
-        if key in tr:
-            traffic = tr[key]
+        ent = tr.get(f"{args.precision}:{dom}")
+        if ent:
+            with open(os.path.join(ROOT, ent["kernel_source"]), "rb") as f:
+                same = hashlib.sha1(f.read()).hexdigest() == ent["source_sha1"]
+            traffic = ent["dram_bytes_per_launch"] if same else None
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel_class": dom,
                 "launches": n_l, "ms_per_batch": ms, "peak_source": note,
