@@ -125,6 +125,27 @@ class ClockSampler:
 
 # --------------------------------------------------------------- workload
 
+def rank_slice(rank, per_rank):
+    """Weak scaling: rank r owns instances r*B .. r*B+B-1 (first, count)."""
+    return rank * per_rank, per_rank
+
+
+def max_over_ranks(x, world, device=None):
+    """Max of a float over ranks: the job takes as long as its slowest rank."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(per_rank, world, steps, seconds):
+    """Contractions per second of the whole job."""
+    return per_rank * world * steps / seconds
+
+
 def make_instances(first, count, size):
     from workloads import ising
     return [ising.lattice2d(size, size, 0.5, "gauss", seed=2 * 10**6 + first + i)
@@ -231,8 +252,8 @@ def bench_ours(args):
             "bf16": B.TN_PREC_BF16}[args.precision]
     Bn, K, W = args.batch, args.steps, args.warmup
 
-    # workload (rank r owns instances r*B .. r*B+B-1)
-    ws = make_instances(rank * Bn, Bn, args.size)
+    first, _ = rank_slice(rank, Bn)
+    ws = make_instances(first, Bn, args.size)
     w0 = ws[0]
     plan = B.tn_plan(w0["n"], w0["edges"], np.full(len(w0["edges"]), 2), args.chi,
                      env_size=args.size)
@@ -284,12 +305,8 @@ def bench_ours(args):
     launches = B.tn_ctx_profile(ctx)
     gpu_launches = int(sum(v[0] for v in launches.values()))
     logz, status = B.tn_logz(ctx, Bn)
-    total_ms = float(sum(times))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = Bn * world * K / (total_ms / 1e3)
+    total_ms = max_over_ranks(float(sum(times)), world, dev)
+    value = whole_job_rate(Bn, world, K, total_ms / 1e3)
 
     # end to end through the host entry point (pinned host buffers)
     pinned = torch.from_numpy(host).pin_memory()
@@ -301,12 +318,8 @@ def bench_ours(args):
     t0 = time.perf_counter()
     for _ in range(K):
         lz_h, st_h = B.tn_contract_approx_host(ctx, plans, hptrs, prec, 0, sh)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": Bn * world * K / e2e_s, "unit": "contractions/s",
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e = {"value": whole_job_rate(Bn, world, K, e2e_s), "unit": "contractions/s",
            "h2d_bytes_per_step": int(8 * elems * Bn), "d2h_bytes_per_step": int(12 * Bn)}
 
     # diagnostic pass: per-kernel-class durations (CUDA events), not timed above
