@@ -426,17 +426,17 @@ __device__ void tridiag_regs_f32(const float* As, int ld, int n, float* R, float
   if (ri == 0) publish(0);
   for (int k = 0; k + 2 < n; ++k) {
     __syncthreads();  // row k published; the previous step's reads of V, W are done
-    const float s = S2[0] + S2[1];
-    const float alpha = X[k + 1];
-    float tk, beta, sc;
-    if (s == 0.f) {
-      tk = 0.f; beta = alpha; sc = 0.f;
-    } else {
-      beta = -copysignf(sqrtf(alpha * alpha + s), alpha);
-      tk = (beta - alpha) / beta;
-      sc = 1.f / (alpha - beta);
-    }
-    if (tid < 128) {
+    if (tid < 128) {  // the first four warps form the reflector (same values in each)
+      const float s = S2[0] + S2[1];
+      const float alpha = X[k + 1];
+      float tk, beta, sc;
+      if (s == 0.f) {
+        tk = 0.f; beta = alpha; sc = 0.f;
+      } else {
+        beta = -copysignf(sqrtf(alpha * alpha + s), alpha);
+        tk = (beta - alpha) / beta;
+        sc = 1.f / (alpha - beta);
+      }
       const int c = tid;
       const float vc = (c == k + 1) ? 1.f : ((c > k + 1 && c < n && tk != 0.f) ? X[c] * sc : 0.f);
       V[c] = vc;
@@ -447,7 +447,8 @@ __device__ void tridiag_regs_f32(const float* As, int ld, int n, float* R, float
         tau[k] = tk;
       }
     }
-    __syncthreads();  // V complete; X free
+    __syncthreads();  // V and tau_k complete; X free
+    const float tk = tau[k];
     const bool rowlive = ri > k && ri < n;
     if (tk != 0.f) {  // uniform across the block
       if (rowlive) {
@@ -486,10 +487,11 @@ __device__ void tridiag_regs_f32(const float* As, int ld, int n, float* R, float
           if (cb + q + 3 <= k || cb + q >= n) continue;  // warp-uniform: group inactive
           const float4 v4 = *reinterpret_cast<const float4*>(V + cb + q);
           const float4 w4 = *reinterpret_cast<const float4*>(W + cb + q);
-          a[q] -= fmaf(vi, w4.x, wi * v4.x);
-          a[q + 1] -= fmaf(vi, w4.y, wi * v4.y);
-          a[q + 2] -= fmaf(vi, w4.z, wi * v4.z);
-          a[q + 3] -= fmaf(vi, w4.w, wi * v4.w);
+          // a -= v_i w_c + w_i v_c as two FMAs
+          a[q] = fmaf(-wi, v4.x, fmaf(-vi, w4.x, a[q]));
+          a[q + 1] = fmaf(-wi, v4.y, fmaf(-vi, w4.y, a[q + 1]));
+          a[q + 2] = fmaf(-wi, v4.z, fmaf(-vi, w4.z, a[q + 2]));
+          a[q + 3] = fmaf(-wi, v4.w, fmaf(-vi, w4.w, a[q + 3]));
         }
       }
     }
