@@ -4,8 +4,9 @@
 // One CTA per matrix, everything in shared memory:
 //   1. Householder reduction to tridiagonal form, A = Q T Q^T
 //      (Golub & Van Loan, Matrix Computations, Sec. 8.3.1);
-//   2. the wanted eigenvalues of T by Sturm-sequence bisection, one thread per
-//      eigenvalue (Barth, Martin & Wilkinson 1967);
+//   2. the wanted eigenvalues of T by Sturm-sequence multisection, four
+//      threads per eigenvalue (Barth, Martin & Wilkinson 1967); in FP32 a first
+//      round on an equispaced grid is shared by all eigenvalues;
 //   3. eigenvectors of T by inverse iteration with partial-pivoting LU of
 //      T - lambda I (Wilkinson), one thread per eigenvector, shifts of
 //      near-equal eigenvalues separated as in LAPACK's stein;
@@ -387,8 +388,11 @@ __device__ __forceinline__ T quad_sum(T v) {
 // FP32 Householder tridiagonalisation with the matrix in registers: thread
 // (row ri = tid & 127, column half h = tid >> 7) holds A[ri][64 h .. 64 h + 63]
 // (zero outside n x n).  Step k: the owners of row k publish it (= column k)
-// to X; every warp forms the reflector from it (same arithmetic, same values)
-// and threads c < 128 write v_c to V (zero outside k+1 .. n-1); the rows'
+// to X, four float4 stores per owner and nothing else, so the next step waits
+// on no serial arithmetic; each of the first four warps sums the squares of
+// the row's tail itself (one float4 per lane and a warp reduction) and forms
+// the reflector (same arithmetic, same values in each), and threads c < 128
+// write v_c to V (zero outside k+1 .. n-1); the rows'
 // partial products p = A v go to P; threads c write w_c = tau p_c - (tau^2 /
 // 2)(v.p) v_c to W (zero outside); then every row updates in place, A -= v
 // w^T + w v^T.  Zeros outside the active block make the inner loops plain
@@ -396,38 +400,37 @@ __device__ __forceinline__ T quad_sum(T v) {
 // R as rows: R[k * kRld + c + (c / 32) * 4] = v_c for c < 128 (zero outside
 // k+1 .. n-1, v_{k+1} = 1; the padding puts the four 32-row quarters in
 // disjoint bank groups); R may overlay As, which is read only at the start.
-// dd, ee, tau as the shared-memory version.  X, V, W (128 each) and P
-// (2 x 128) are 16-byte aligned.
+// dd, ee, tau as the shared-memory version.  X, V, W (128 each, W followed by
+// 16 spare entries) and P (2 x 128) are 16-byte aligned.
 constexpr int kRld = 144;
 __device__ __forceinline__ int rpad(int c) { return c + (c >> 5) * 4; }
 
 __device__ void tridiag_regs_f32(const float* As, int ld, int n, float* R, float* dd, float* ee,
                                  float* tau, float* X, float* V, float* W, float* P) {
-  __shared__ __align__(16) float S2[2], D8[8];  // published row's tail norm; warp partials
+  float* D8 = W + 128;  // warp partials of v . p
   const int tid = threadIdx.x, ri = tid & 127, h = tid >> 7, lane = tid & 31, cb = h * 64;
   float a[64];
 #pragma unroll
   for (int q = 0; q < 64; ++q) a[q] = (ri < n && cb + q < n) ? As[ri * ld + cb + q] : 0.f;
-  // row ri = k is published with sum_{c >= k + 2} A[k][c]^2 over this half
   auto publish = [&](int k) {
-    float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-    for (int q = 0; q < 64; q += 4) {
+    for (int q = 0; q < 64; q += 4)
       *reinterpret_cast<float4*>(X + cb + q) = make_float4(a[q], a[q + 1], a[q + 2], a[q + 3]);
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (cb + q + u >= k + 2) {
-          if (u & 1) s1 = fmaf(a[q + u], a[q + u], s1);
-          else s0 = fmaf(a[q + u], a[q + u], s0);
-        }
-    }
-    S2[h] = s0 + s1;
   };
   if (ri == 0) publish(0);
   for (int k = 0; k + 2 < n; ++k) {
     __syncthreads();  // row k published; the previous step's reads of V, W are done
     if (tid < 128) {  // the first four warps form the reflector (same values in each)
-      const float s = S2[0] + S2[1];
+      float s;
+      {  // sum of squares of row k beyond column k + 1, in every warp
+        const float4 x4 = *reinterpret_cast<const float4*>(X + 4 * lane);
+        const int c0 = 4 * lane;
+        float t = (c0 >= k + 2) ? x4.x * x4.x : 0.f;
+        t = (c0 + 1 >= k + 2) ? fmaf(x4.y, x4.y, t) : t;
+        t = (c0 + 2 >= k + 2) ? fmaf(x4.z, x4.z, t) : t;
+        t = (c0 + 3 >= k + 2) ? fmaf(x4.w, x4.w, t) : t;
+        s = warp_sum(t);
+      }
       const float alpha = X[k + 1];
       float tk, beta, sc;
       if (s == 0.f) {
@@ -513,6 +516,36 @@ __device__ void tridiag_regs_f32(const float* As, int ld, int n, float* R, float
   __syncthreads();
 }
 
+// FP32 multisection: Sturm sequences per thread and rounds after the shared
+// grid round; 257 (4 kSturmIlp + 1)^kSturmRounds >= 5^12 keeps the final
+// interval at or below that of twelve quinsection rounds.  One sequence per
+// thread measured fastest with two CTAs per SM: more interleaved sequences
+// cost more issue slots than their overlapped divisions save.
+constexpr int kSturmIlp = 1;
+constexpr int kSturmRounds = 9;
+
+// Sturm counts (eigenvalues of T below x[i]) of several shifts, interleaved so
+// that the divisions of independent sequences overlap.
+__device__ void sturm_count_multi(const float* dd, const float* e2, int n, const float* x,
+                                  float pivmin, int* c) {
+  float q[kSturmIlp];
+#pragma unroll
+  for (int i = 0; i < kSturmIlp; ++i) {
+    q[i] = dd[0] - x[i];
+    if (fabsf(q[i]) < pivmin) q[i] = -pivmin;
+    c[i] = (q[i] < 0.f);
+  }
+  for (int j = 1; j < n; ++j) {
+    const float d = dd[j], e = e2[j - 1];
+#pragma unroll
+    for (int i = 0; i < kSturmIlp; ++i) {
+      q[i] = d - x[i] - __fdividef(e, q[i]);
+      if (fabsf(q[i]) < pivmin) q[i] = -pivmin;
+      c[i] += (q[i] < 0.f);
+    }
+  }
+}
+
 template <typename T>
 __device__ int sturm_count_fast(const T* dd, const T* e2, int n, T x, T pivmin) {
   T q = dd[0] - x;
@@ -534,15 +567,16 @@ __device__ int sturm_count_fast(const T* dd, const T* e2, int n, T x, T pivmin) 
 // vectors (one barrier per vector), then U = H_0 ... H_{n-3} Z from the
 // padded reflector rows R, then signs (largest-|.| entry, first on ties,
 // positive) and the stores U (n x r) and Ut (r x n).
-__device__ void vectors_f32(const float* Zs, int zld, int n, int r, const float* R,
-                            const float* tau, float* pub, float* U, float* Ut) {
+__device__ void vectors_f32(const float* Zs, int zld, const float* zscale, int n, int r,
+                            const float* R, const float* tau, float* pub, float* U, float* Ut) {
   const int tid = threadIdx.x, col = tid >> 2, qr = tid & 3;
   const bool live = col < r;
+  const float zs = live ? zscale[col] : 0.f;
   float z[kQ];
 #pragma unroll
   for (int kk = 0; kk < kQ; ++kk) {
     const int row = qr * kQ + kk;
-    z[kk] = (live && row < n) ? Zs[col * zld + row] : 0.f;
+    z[kk] = (live && row < n) ? Zs[col * zld + row] * zs : 0.f;
   }
   auto load = [&](const float* src, float* v) {
 #pragma unroll
@@ -551,11 +585,20 @@ __device__ void vectors_f32(const float* Zs, int zld, int n, int r, const float*
       v[4 * m] = t.x; v[4 * m + 1] = t.y; v[4 * m + 2] = t.z; v[4 * m + 3] = t.w;
     }
   };
-  auto normalise_publish = [&](float* dst) {
-    float s = 0.f;
+  // dot product of 32 register entries as four interleaved partial sums
+  auto dot32 = [](const float* x, const float* y) {
+    float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
 #pragma unroll
-    for (int kk = 0; kk < kQ; ++kk) s = fmaf(z[kk], z[kk], s);
-    s = quad_sum(s);
+    for (int kk = 0; kk < kQ; kk += 4) {
+      d0 = fmaf(x[kk], y[kk], d0);
+      d1 = fmaf(x[kk + 1], y[kk + 1], d1);
+      d2 = fmaf(x[kk + 2], y[kk + 2], d2);
+      d3 = fmaf(x[kk + 3], y[kk + 3], d3);
+    }
+    return (d0 + d1) + (d2 + d3);
+  };
+  auto normalise_publish = [&](float* dst) {
+    float s = quad_sum(dot32(z, z));
     const float inv = (s > 0.f) ? 1.f / sqrtf(s) : 0.f;
 #pragma unroll
     for (int kk = 0; kk < kQ; ++kk) z[kk] *= inv;
@@ -570,10 +613,7 @@ __device__ void vectors_f32(const float* Zs, int zld, int n, int r, const float*
     if (live && col > j) {
       float p[kQ];
       load(pub + (j & 1) * kRld, p);
-      float d = 0.f;
-#pragma unroll
-      for (int kk = 0; kk < kQ; ++kk) d = fmaf(p[kk], z[kk], d);
-      d = quad_sum(d);
+      const float d = quad_sum(dot32(p, z));
 #pragma unroll
       for (int kk = 0; kk < kQ; ++kk) z[kk] = fmaf(-d, p[kk], z[kk]);
       if (col == j + 1) normalise_publish(pub + ((j + 1) & 1) * kRld);
@@ -585,10 +625,7 @@ __device__ void vectors_f32(const float* Zs, int zld, int n, int r, const float*
       if (tk == 0.f) continue;
       float v[kQ];
       load(R + k * kRld, v);
-      float d = 0.f;
-#pragma unroll
-      for (int kk = 0; kk < kQ; ++kk) d = fmaf(v[kk], z[kk], d);
-      d = quad_sum(d) * tk;
+      const float d = quad_sum(dot32(v, z)) * tk;
 #pragma unroll
       for (int kk = 0; kk < kQ; ++kk) z[kk] = fmaf(-d, v[kk], z[kk]);
     }
@@ -784,10 +821,55 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
   const T gl = scal[1], gu = scal[2], tnorm = scal[3], pivmin = scal[4];
   const T eps = Lim<T>::eps();
 
-  // ---- 2. multisection: 4 threads per eigenvalue, interval shrinks 5x per round
-  {
+  // ---- 2. multisection: 4 threads per eigenvalue
+  if constexpr (sizeof(T) == 4) {
+    // each thread evaluates kSturmIlp interleaved Sturm sequences, so a round
+    // cuts the interval into P + 1 = 4 kSturmIlp + 1 parts; the quad counts
+    // the points at or below eigenvalue j (counts are monotone in x) and keeps
+    // the part between the last such point and the next
+    constexpr int P = 4 * kSturmIlp;
     const int q = tid & 3;
-    const int rounds = (sizeof(T) == 8) ? 24 : 12;
+    // a first round shared by all eigenvalues: counts at kThreads equispaced
+    // points give each one a starting interval of width (gu - gl) / (kThreads + 1)
+    int* gcnt = reinterpret_cast<int*>(part);
+    const float hg = (gu - gl) / float(kThreads + 1);
+    gcnt[tid] = sturm_count_fast(dd, e2, n, fmaf(hg, float(tid + 1), gl), pivmin);
+    __syncthreads();
+    for (int base = 0; base < nl; base += kThreads / 4) {
+      const int t = base + (tid >> 2);
+      const bool valid = (t < nl) && (t < n);
+      const int j = n - 1 - t;
+      int m0 = 0, m1 = kThreads;  // first grid point whose count exceeds j
+      for (int it = 0; it < 9; ++it) {  // 257 outcomes; mid < m1 <= kThreads
+        if (m0 >= m1) break;
+        const int mid = (m0 + m1) >> 1;
+        if (gcnt[mid] <= j) m0 = mid + 1;
+        else m1 = mid;
+      }
+      float lo = (m0 > 0) ? fmaf(hg, float(m0), gl) : gl;
+      float hi = (m0 < kThreads) ? fmaf(hg, float(m0 + 1), gl) : gu;
+      for (int it = 0; it < kSturmRounds; ++it) {
+        const float h = (hi - lo) / float(P + 1);
+        float xs[kSturmIlp];
+        int cnt[kSturmIlp];
+#pragma unroll
+        for (int i = 0; i < kSturmIlp; ++i) xs[i] = fmaf(h, float(q + 4 * i + 1), lo);
+        if (valid) sturm_count_multi(dd, e2, n, xs, pivmin, cnt);
+        int m = 0;
+#pragma unroll
+        for (int i = 0; i < kSturmIlp; ++i) m += (valid && cnt[i] <= j);
+        m += __shfl_xor_sync(0xffffffffu, m, 1);
+        m += __shfl_xor_sync(0xffffffffu, m, 2);
+        const float nlo = (m > 0) ? fmaf(h, float(m), lo) : lo;
+        hi = (m < P) ? fmaf(h, float(m + 1), lo) : hi;
+        lo = nlo;
+      }
+      if (valid && q == 0) lam[t] = 0.5f * (lo + hi);
+    }
+  } else {
+    // interval shrinks 5x per round
+    const int q = tid & 3;
+    const int rounds = 24;
     for (int base = 0; base < nl; base += kThreads / 4) {
       const int t = base + (tid >> 2);
       const bool valid = (t < nl) && (t < n);
@@ -829,11 +911,16 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
   // pseudo-random vector, the second from its normalised result, so the
   // contamination by other eigenvectors falls like (eps ||T|| / gap)^2;
   // clusters are separated by the Gram-Schmidt pass below.  y and x live in
-  // this thread's padded shared-memory column, the triangular factor in local
-  // memory.
+  // this thread's padded shared-memory column, the triangular factor (each
+  // row divided by its pivot) in local memory.  The pivot choice is made by
+  // selects, so the lanes of a warp never diverge.  The solve grows like
+  // 1 / (eps ||T||) and L_v carries an arbitrary overall scale, so each
+  // solution is brought to max-abs 1 (before Gram-Schmidt squares it) by its
+  // reader: the second solve and the vector load take y times vscale.
   const int zld = n + 1;
+  T* vscale = shift;  // shift[tid] is read once, before the solves
   if (tid < r) {
-    T u1[kNmax], u2[kNmax], u3[kNmax];
+    T u2[kNmax], u3[kNmax];
     T* y = Zs + tid * zld;
     auto start = [&](int k) {
       unsigned int h = 2654435761u * (unsigned)(k + 1) ^ (40503u * (unsigned)(tid + 7));
@@ -842,60 +929,56 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
     };
     const T lmb = shift[tid];
     const T tp = fmax(eps * tnorm, Lim<T>::safmin());
+    T inv = T(1);  // max-abs normalisation of the previous solve's result
     for (int it = 0; it < 2; ++it) {
     T a = dd[0] - lmb;
     T bb = (n > 1) ? ee[0] : T(0);
-    T yk = (it == 0) ? start(0) : y[0];
+    T yk = (it == 0) ? start(0) : y[0] * inv;
     for (int k = 0; k + 1 < n; ++k) {
       const T c = ee[k];
       const T nd = dd[k + 1] - lmb;
       const T ns = (k + 2 < n) ? ee[k + 1] : T(0);
-      const T yn = (it == 0) ? start(k + 1) : y[k + 1];
-      if (fabs(a) >= fabs(c)) {
-        if (a == T(0)) a = tp;
-        const T mlt = fdiv(c, a);
-        u1[k] = a; u2[k] = bb; u3[k] = T(0);
-        y[k] = yk;
-        yk = yn - mlt * yk;
-        a = nd - mlt * bb;
-        bb = ns;
-      } else {
-        const T mlt = fdiv(a, c);
-        u1[k] = c; u2[k] = nd; u3[k] = ns;
-        y[k] = yn;
-        yk = yk - mlt * yn;
-        a = bb - mlt * nd;
-        bb = -mlt * ns;
-      }
+      const T yn = (it == 0) ? start(k + 1) : y[k + 1] * inv;
+      // pivot on row k when |a| >= |c| (then a == 0 implies c == 0: use tp)
+      const bool piv = fabs(a) >= fabs(c);
+      const T den = piv ? ((a == T(0)) ? tp : a) : c;
+      const T rd = fdiv(T(1), den);
+      const T mlt = (piv ? c : a) * rd;
+      const T yo = piv ? yk : yn, ye = piv ? yn : yk;
+      u2[k] = (piv ? bb : nd) * rd;
+      u3[k] = piv ? T(0) : ns * rd;
+      y[k] = yo * rd;
+      yk = ye - mlt * yo;
+      a = piv ? (nd - mlt * bb) : (bb - mlt * nd);
+      bb = piv ? ns : -mlt * ns;
     }
     if (a == T(0)) a = tp;
-    u1[n - 1] = a;
     T x2 = fdiv(yk, a);  // x_{k+2}, x_{k+1} rolling
     y[n - 1] = x2;
     T x1 = x2;
+    T mx = fabs(x2);
     if (n >= 2) {
-      x1 = fdiv(y[n - 2] - u2[n - 2] * x2, u1[n - 2]);
+      x1 = y[n - 2] - u2[n - 2] * x2;
       y[n - 2] = x1;
+      mx = fmax(mx, fabs(x1));
     }
-#pragma unroll 4
+#pragma unroll 16
     for (int k = n - 3; k >= 0; --k) {
-      const T xk = fdiv(y[k] - u2[k] * x1 - u3[k] * x2, u1[k]);
+      const T xk = y[k] - u2[k] * x1 - u3[k] * x2;
       y[k] = xk;
+      mx = fmax(mx, fabs(xk));
       x2 = x1;
       x1 = xk;
     }
-    // the solve grows like 1 / (eps ||T||) and L_v carries an arbitrary
-    // overall scale: bring the vector to max-abs 1 before Gram-Schmidt squares it
-    T mx = T(0);
-    for (int k = 0; k < n; ++k) mx = fmax(mx, fabs(y[k]));
-    const T inv = (mx > T(0) && isfinite(mx)) ? T(1) / mx : T(1);
-    for (int k = 0; k < n; ++k) y[k] *= inv;
+    inv = (mx > T(0) && isfinite(mx)) ? T(1) / mx : T(1);
     }  // two solves: contamination (eps ||T|| / gap)^2
+    vscale[tid] = inv;
   }
   __syncthreads();
 
   if constexpr (sizeof(T) == 4) {
-    vectors_f32(reinterpret_cast<const float*>(Zs), zld, n, r,
+    vectors_f32(reinterpret_cast<const float*>(Zs), zld,
+                reinterpret_cast<const float*>(vscale), n, r,
                 reinterpret_cast<const float*>(A), reinterpret_cast<const float*>(tau),
                 reinterpret_cast<float*>(pub), reinterpret_cast<float*>(Ug) + (long long)b * sU,
                 Utg ? reinterpret_cast<float*>(Utg) + (long long)b * sUt : nullptr);
@@ -907,7 +990,7 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
 #pragma unroll
   for (int kk = 0; kk < kQ; ++kk) {
     const int row = kk * 4 + qr;
-    z[kk] = (live && row < n) ? Zs[col * zld + row] : T(0);
+    z[kk] = (live && row < n) ? Zs[col * zld + row] * vscale[col] : T(0);
   }
   // modified Gram-Schmidt in descending eigenvalue order
   for (int j = 0; j < r; ++j) {
