@@ -692,23 +692,29 @@ void run_plan_tc(tn_ctx* c, const tn_plan_t* P, int B, const double* const* tens
   float* Snext = w.S1;
   for (size_t s = 0; s < P->steps.size(); ++s) {
     const tn::Step& st = P->steps[s];
-    int maxe = 1, maxdl = 1, maxj = 1, maxt = 1;
+    int maxe = 1, maxdl = 1, maxj = 1, maxt = 1, maxa = 1, maxb = 1, other = 0;
     for (int k = 0; k < st.n; ++k) {
       const tn::SiteOp& o = st.site[k];
       maxe = std::max<int>(maxe, o.a * o.dhl * o.de * o.b * o.dhr);
       maxdl = std::max<int>(maxdl, o.a * o.dhl);
       maxj = std::max<int>(maxj, o.de * o.b * o.dhr);
       maxt = std::max<int>(maxt, o.dp * o.dhl * o.dhr * o.de);
+      maxa = std::max<int>(maxa, o.a);
+      maxb = std::max<int>(maxb, o.b);
+      if (o.dp != 2 || o.dhl != 2 || o.dhr != 2 || o.de != 2 || lay[s].y_off[k] % 2 != 0) ++other;
     }
+    const int bond2 = (other <= 2) ? 1 : 0;  // square-lattice rows: only the end sites differ
     if (st.kind == 0) {
       Scope(c, TN_KC_FUSE, strm),
-      ck(tn::launch_fuse_f32(tabs[s].fuse, st.n, maxe, maxdl, maxj, maxt, tens_table, w.inv,
+      ck(tn::launch_fuse_f32(tabs[s].fuse, st.n, maxe, maxdl, maxj, maxt, maxa, maxb, bond2,
+                             tens_table, w.inv,
                              P->n_vertices, nullptr, 0, 1, Snext, w.sS, nullptr, nullptr, B, strm),
          "fuse");
       std::swap(Scur, Snext);
     } else if (st.kind == 1) {
       Scope(c, TN_KC_FUSE, strm),
-      ck(tn::launch_fuse_f32(tabs[s].fuse, st.n, maxe, maxdl, maxj, maxt, tens_table, w.inv,
+      ck(tn::launch_fuse_f32(tabs[s].fuse, st.n, maxe, maxdl, maxj, maxt, maxa, maxb, bond2,
+                             tens_table, w.inv,
                              P->n_vertices, Scur, w.sS, 0, w.Y, w.sY, w.Yt, tabs[s].y_off, B,
                              strm),
          "fuse");
@@ -717,7 +723,8 @@ void run_plan_tc(tn_ctx* c, const tn_plan_t* P, int B, const double* const* tens
       std::swap(Scur, Snext);
     } else {
       Scope(c, TN_KC_FUSE, strm),
-      ck(tn::launch_fuse_f32(tabs[s].fuse, st.n, maxe, maxdl, maxj, maxt, tens_table, w.inv,
+      ck(tn::launch_fuse_f32(tabs[s].fuse, st.n, maxe, maxdl, maxj, maxt, maxa, maxb, bond2,
+                             tens_table, w.inv,
                              P->n_vertices, Scur, w.sS, 0, w.Y, w.sY, nullptr, nullptr, B, strm),
          "fuse");
       int maxD = 1;

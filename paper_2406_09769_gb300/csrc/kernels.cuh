@@ -83,8 +83,11 @@ cudaError_t launch_eigh_top(const T* L, long long sL, T* U, long long sU, T* Ut,
                             int batch, cudaStream_t st);
 
 // FP32-storage kernels of the mixed-precision path (see kernels_f32.cu).
+// bond2: all sites but at most two (a row's end sites) have dp = dhl = dhr =
+// de = 2 and even Y offsets; max_a, max_b: largest a and b over the sites.
 cudaError_t launch_fuse_f32(const FuseSite* sites, int n, int max_elems, int max_dl, int max_j,
-                            int max_t, const double* const* tens,
+                            int max_t, int max_a, int max_b, int bond2,
+                            const double* const* tens,
                             const double* inv_norm, int nv, const float* S, long long sS,
                             int trivial, float* Y, long long sY, float* Yt, const int64_t* yt_off,
                             int batch, cudaStream_t st);

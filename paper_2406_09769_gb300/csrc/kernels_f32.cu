@@ -214,6 +214,101 @@ __global__ void __launch_bounds__(256) k_fuse_f32_wide(const FuseSite* __restric
   }
 }
 
+// The same fusion when every bond of the site is of dimension 2 (dp = dhl =
+// dhr = de = 2: Dl = 2a, Dr = 2b, J = 4b), as on the square lattices.  Block
+// of 256 threads owns a = aa0 .. aa0 + 15 and b = bb0 .. bb0 + 63; thread (x,
+// y) = (tid % 64, tid / 64) reads S[aa, 0, bb] and S[aa, 1, bb] for bb = bb0 +
+// x and aa = aa0 + y + 4 m (m = 0..3) and forms the 2 x 2 x 2 block
+// Y[2 aa + hl][e * 2b + 2 bb + hr] from the 16 site-tensor entries held in
+// registers: each S value feeds eight outputs, and the hr pairs are float2
+// stores (consecutive threads write consecutive pairs of one row).  Yt is
+// written from a shared tile [32 rows a'][2 x 128 columns j] (pitch 258:
+// float2-aligned rows) along a', 32 consecutive a' per warp store.  A site
+// with other bond dimensions or an odd Y offset (the end sites of a row have
+// dhl = 1 or dhr = 1) takes a plain per-element path over the same (a, b)
+// range.  grid: (ceil(max b / 64), ceil(max a / 16), sites * batch).
+constexpr int kFuseD2Pitch = 258;
+__global__ void __launch_bounds__(256) k_fuse_f32_d2(const FuseSite* __restrict__ sites,
+                                                     int n_sites, const double* const* tens,
+                                                     const double* __restrict__ inv_norm, int nv,
+                                                     const float* __restrict__ S, long long sS,
+                                                     float* __restrict__ Y, long long sY,
+                                                     float* __restrict__ Yt,
+                                                     const int64_t* yt_off) {
+  __shared__ __align__(16) float tile[32 * kFuseD2Pitch];
+  const int site = blockIdx.z % n_sites, i = blockIdx.z / n_sites;
+  const FuseSite f = sites[site];
+  const int bb0 = blockIdx.x * 64, aa0 = blockIdx.y * 16;
+  if (bb0 >= f.b || aa0 >= f.a) return;  // uniform per block
+  const int tid = threadIdx.x, x = tid & 63, y = tid >> 6;
+  const double* Tb = tens[i] + f.t_off;
+  const float inv = float(inv_norm[(long long)i * nv + f.vertex]);
+  const float* Si = S + (long long)i * sS + f.s_off;
+  float* Yi = Y + (long long)i * sY + f.y_off;
+  float* Yti = Yt + (long long)i * sY + yt_off[site];
+  if (f.dp != 2 || f.dhl != 2 || f.dhr != 2 || f.de != 2 || (f.y_off & 1) || (yt_off[site] & 1)) {
+    const int Dl = f.a * f.dhl, Dr = f.b * f.dhr, J = f.de * Dr;
+    const int per = f.dhl * f.dhr * f.de;
+    for (int q = tid; q < 16 * 64 * per; q += 256) {
+      int r = q;
+      const int e = r % f.de; r /= f.de;
+      const int hr = r % f.dhr; r /= f.dhr;
+      const int hl = r % f.dhl; r /= f.dhl;
+      const int bb = bb0 + r % 64, aa = aa0 + r / 64;
+      if (aa >= f.a || bb >= f.b) continue;
+      const double* T = Tb + hl * f.shl + hr * f.shr + e * f.se;
+      const float* Sk = Si + (long long)aa * f.dp * f.b + bb;
+      float acc = 0.f;
+      for (int p = 0; p < f.dp; ++p) acc = fmaf(Sk[(long long)p * f.b], float(T[p * f.sp]), acc);
+      const float v = acc * inv;
+      const int ap = aa * f.dhl + hl, j = e * Dr + bb * f.dhr + hr;
+      Yi[(long long)ap * J + j] = v;
+      Yti[(long long)j * Dl + ap] = v;
+    }
+    return;  // uniform per block
+  }
+  const int Dl = 2 * f.a, J = 4 * f.b;
+  float t[2][2][2][2];  // [p][hl][hr][e]
+#pragma unroll
+  for (int p = 0; p < 2; ++p)
+#pragma unroll
+    for (int hl = 0; hl < 2; ++hl)
+#pragma unroll
+      for (int hr = 0; hr < 2; ++hr)
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+          t[p][hl][hr][e] = float(Tb[p * f.sp + hl * f.shl + hr * f.shr + e * f.se]);
+  const int bb = bb0 + x;
+  const bool bok = bb < f.b;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int al = y + 4 * m, aa = aa0 + al;
+    const bool ok = bok && aa < f.a;
+    const float s0 = ok ? Si[(long long)aa * 2 * f.b + bb] : 0.f;
+    const float s1 = ok ? Si[(long long)aa * 2 * f.b + f.b + bb] : 0.f;
+#pragma unroll
+    for (int hl = 0; hl < 2; ++hl)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        // sum over p in the order of the other fusion kernels, then the site norm
+        const float v0 = fmaf(s1, t[1][hl][0][e], s0 * t[0][hl][0][e]) * inv;
+        const float v1 = fmaf(s1, t[1][hl][1][e], s0 * t[0][hl][1][e]) * inv;
+        const float2 v = make_float2(v0, v1);
+        if (ok)
+          *reinterpret_cast<float2*>(Yi + (long long)(2 * aa + hl) * J + e * 2 * f.b + 2 * bb) = v;
+        *reinterpret_cast<float2*>(tile + (2 * al + hl) * kFuseD2Pitch + e * 128 + 2 * x) = v;
+      }
+  }
+  __syncthreads();
+  // Yt[j][a'] for the block's 2 x 128 columns j and 32 rows a'
+  const int lane = tid & 31, w = tid >> 5, ap = 2 * aa0 + lane;
+  for (int jl = w; jl < 256; jl += 8) {
+    const int e = jl >> 7, c = jl & 127;  // column 2 bb0 + c of half e
+    if (2 * bb0 + c < 2 * f.b && ap < Dl)
+      Yti[(long long)(e * 2 * f.b + 2 * bb0 + c) * Dl + ap] = tile[lane * kFuseD2Pitch + jl];
+  }
+}
+
 __global__ void k_fill_env_root_f32(float* R, long long sR, unsigned int* amax, long long s_amax,
                                     int batch) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -342,11 +437,17 @@ cudaError_t launch_sgemm_nt(const TcGemmArgs& g, cudaStream_t st) {
 }
 
 cudaError_t launch_fuse_f32(const FuseSite* sites, int n, int max_elems, int max_dl, int max_j,
-                            int max_t, const double* const* tens,
+                            int max_t, int max_a, int max_b, int bond2,
+                            const double* const* tens,
                             const double* inv_norm, int nv, const float* S, long long sS,
                             int trivial, float* Y, long long sY, float* Yt, const int64_t* yt_off,
                             int batch, cudaStream_t st) {
   if (Yt && !trivial && max_dl > 0 && max_j > 0) {
+    if (bond2 && sY % 2 == 0 && max_a > 0 && max_b > 0) {
+      dim3 grid((max_b + 63) / 64, (max_a + 15) / 16, n * batch);
+      k_fuse_f32_d2<<<grid, 256, 0, st>>>(sites, n, tens, inv_norm, nv, S, sS, Y, sY, Yt, yt_off);
+      return cudaGetLastError();
+    }
     if (max_t <= kFuseT) {
       dim3 grid((max_j + 127) / 128, (max_dl + 31) / 32, n * batch);
       k_fuse_f32_wide<<<grid, 256, 0, st>>>(sites, n, tens, inv_norm, nv, S, sS, Y, sY, Yt,
