@@ -455,17 +455,15 @@ __device__ void tridiag_regs_f32(const float* As, int ld, int n, float* R, float
     const bool rowlive = ri > k && ri < n;
     if (tk != 0.f) {  // uniform across the block
       if (rowlive) {
-        float p0 = 0.f, p1 = 0.f;
+        float2 pq = make_float2(0.f, 0.f);  // (even, odd) columns, packed FMAs
 #pragma unroll
         for (int q = 0; q < 64; q += 4) {
           if (cb + q + 3 <= k || cb + q >= n) continue;  // warp-uniform: group inactive
           const float4 v4 = *reinterpret_cast<const float4*>(V + cb + q);
-          p0 = fmaf(a[q], v4.x, p0);
-          p1 = fmaf(a[q + 1], v4.y, p1);
-          p0 = fmaf(a[q + 2], v4.z, p0);
-          p1 = fmaf(a[q + 3], v4.w, p1);
+          pq = __ffma2_rn(make_float2(a[q], a[q + 1]), make_float2(v4.x, v4.y), pq);
+          pq = __ffma2_rn(make_float2(a[q + 2], a[q + 3]), make_float2(v4.z, v4.w), pq);
         }
-        P[h * 128 + ri] = p0 + p1;
+        P[h * 128 + ri] = pq.x + pq.y;
       }
       // v . p folded per warp (rows outside k+1 .. n-1 have v = 0)
       {
@@ -485,16 +483,18 @@ __device__ void tridiag_regs_f32(const float* As, int ld, int n, float* R, float
       __syncthreads();  // W complete
       if (rowlive) {
         const float vi = V[ri], wi = W[ri];
+        const float2 nvi = make_float2(-vi, -vi), nwi = make_float2(-wi, -wi);
 #pragma unroll
         for (int q = 0; q < 64; q += 4) {
           if (cb + q + 3 <= k || cb + q >= n) continue;  // warp-uniform: group inactive
           const float4 v4 = *reinterpret_cast<const float4*>(V + cb + q);
           const float4 w4 = *reinterpret_cast<const float4*>(W + cb + q);
-          // a -= v_i w_c + w_i v_c as two FMAs
-          a[q] = fmaf(-wi, v4.x, fmaf(-vi, w4.x, a[q]));
-          a[q + 1] = fmaf(-wi, v4.y, fmaf(-vi, w4.y, a[q + 1]));
-          a[q + 2] = fmaf(-wi, v4.z, fmaf(-vi, w4.z, a[q + 2]));
-          a[q + 3] = fmaf(-wi, v4.w, fmaf(-vi, w4.w, a[q + 3]));
+          // a -= v_i w_c + w_i v_c as two FMAs, two columns per packed FMA
+          float2 lo = __ffma2_rn(nvi, make_float2(w4.x, w4.y), make_float2(a[q], a[q + 1]));
+          float2 hi = __ffma2_rn(nvi, make_float2(w4.z, w4.w), make_float2(a[q + 2], a[q + 3]));
+          lo = __ffma2_rn(nwi, make_float2(v4.x, v4.y), lo);
+          hi = __ffma2_rn(nwi, make_float2(v4.z, v4.w), hi);
+          a[q] = lo.x; a[q + 1] = lo.y; a[q + 2] = hi.x; a[q + 3] = hi.y;
         }
       }
     }
@@ -585,17 +585,25 @@ __device__ void vectors_f32(const float* Zs, int zld, const float* zscale, int n
       v[4 * m] = t.x; v[4 * m + 1] = t.y; v[4 * m + 2] = t.z; v[4 * m + 3] = t.w;
     }
   };
-  // dot product of 32 register entries as four interleaved partial sums
+  // dot product of 32 register entries as four interleaved partial sums (two
+  // packed pairs); z -= d x in packed pairs
   auto dot32 = [](const float* x, const float* y) {
-    float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+    float2 da = make_float2(0.f, 0.f), db = make_float2(0.f, 0.f);
 #pragma unroll
     for (int kk = 0; kk < kQ; kk += 4) {
-      d0 = fmaf(x[kk], y[kk], d0);
-      d1 = fmaf(x[kk + 1], y[kk + 1], d1);
-      d2 = fmaf(x[kk + 2], y[kk + 2], d2);
-      d3 = fmaf(x[kk + 3], y[kk + 3], d3);
+      da = __ffma2_rn(make_float2(x[kk], x[kk + 1]), make_float2(y[kk], y[kk + 1]), da);
+      db = __ffma2_rn(make_float2(x[kk + 2], x[kk + 3]), make_float2(y[kk + 2], y[kk + 3]), db);
     }
-    return (d0 + d1) + (d2 + d3);
+    return (da.x + da.y) + (db.x + db.y);
+  };
+  auto axpy32 = [](float d, const float* x, float* y) {
+    const float2 nd = make_float2(-d, -d);
+#pragma unroll
+    for (int kk = 0; kk < kQ; kk += 2) {
+      const float2 t = __ffma2_rn(nd, make_float2(x[kk], x[kk + 1]), make_float2(y[kk], y[kk + 1]));
+      y[kk] = t.x;
+      y[kk + 1] = t.y;
+    }
   };
   auto normalise_publish = [&](float* dst) {
     float s = quad_sum(dot32(z, z));
@@ -614,8 +622,7 @@ __device__ void vectors_f32(const float* Zs, int zld, const float* zscale, int n
       float p[kQ];
       load(pub + (j & 1) * kRld, p);
       const float d = quad_sum(dot32(p, z));
-#pragma unroll
-      for (int kk = 0; kk < kQ; ++kk) z[kk] = fmaf(-d, p[kk], z[kk]);
+      axpy32(d, p, z);
       if (col == j + 1) normalise_publish(pub + ((j + 1) & 1) * kRld);
     }
   }
@@ -626,8 +633,7 @@ __device__ void vectors_f32(const float* Zs, int zld, const float* zscale, int n
       float v[kQ];
       load(R + k * kRld, v);
       const float d = quad_sum(dot32(v, z)) * tk;
-#pragma unroll
-      for (int kk = 0; kk < kQ; ++kk) z[kk] = fmaf(-d, v[kk], z[kk]);
+      axpy32(d, v, z);
     }
     float best = -1.f;
     int bi = kNmax;
