@@ -703,13 +703,20 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
   const int b = blockIdx.x;
   const T* L = Lg + (long long)b * sL;
 
+  // L copied row by row with coalesced loads, then symmetrised in place,
+  // A = (L + L^T) / 2: the pair {a, c}, a <= c, by one thread (same values as
+  // forming each element from L directly; the column reads have pitch n + 1)
   bool bad = false;
-  for (int idx = tid; idx < n * n; idx += kThreads) {
-    const int a = idx / n, c = idx % n;
-    const T x = T(0.5) * (L[(long long)a * n + c] + L[(long long)c * n + a]);
-    if (!isfinite(x)) bad = true;
-    A[a * ld + c] = x;
-  }
+  for (int a = warp; a < n; a += kThreads / 32)
+    for (int c = lane; c < n; c += 32) A[a * ld + c] = L[(long long)a * n + c];
+  __syncthreads();
+  for (int a = warp; a < n; a += kThreads / 32)
+    for (int c = a + lane; c < n; c += 32) {
+      const T x = T(0.5) * (A[a * ld + c] + A[c * ld + a]);
+      if (!isfinite(x)) bad = true;
+      A[a * ld + c] = x;
+      A[c * ld + a] = x;
+    }
   if (__syncthreads_or(bad)) {
     for (int idx = tid; idx < n * r; idx += kThreads) Ug[(long long)b * sU + idx] = T(0);
     if (Utg)
