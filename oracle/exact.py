@@ -3,6 +3,7 @@
 Plain definitions only:
   * Z of the Ising model as the spin sum of Sec. 7.1,
     Z = sum_s prod_{(i,j) in E} exp(beta J_ij s_i s_j)   (brute force),
+  * Z of the q-state Potts model, sum_s prod exp(beta J_ij [s_i == s_j]) (brute force),
   * the row-to-row transfer matrix of an open Lx x Ly lattice (textbook),
   * closed forms for trees and cycles,
   * dense contraction of a whole tensor network with einsum (for tiny cases).
@@ -23,6 +24,28 @@ def ising_logz_bruteforce(n_vertices, edges, J, beta, chunk=1 << 18):
         idx = np.arange(start, min(total, start + chunk), dtype=np.int64)
         spins = 1.0 - 2.0 * ((idx[:, None] >> np.arange(n)[None, :]) & 1)
         energy = (spins[:, edges[:, 0]] * spins[:, edges[:, 1]]) @ J
+        a = beta * energy
+        m = a.max()
+        parts.append(m + np.log(np.exp(a - m).sum()))
+    parts = np.asarray(parts)
+    m = parts.max()
+    return float(m + np.log(np.exp(parts - m).sum()))
+
+
+def potts_logz_bruteforce(n_vertices, edges, J, beta, q, chunk=1 << 17):
+    """ln Z of the q-state Potts model by summing all q^n configurations."""
+    n = int(n_vertices)
+    if q ** n > 1 << 24:
+        raise ValueError("brute force limited to 2^24 configurations")
+    edges = np.asarray(edges, dtype=np.int64)
+    J = np.asarray(J, dtype=np.float64)
+    total = q ** n
+    place = q ** np.arange(n, dtype=np.int64)
+    parts = []
+    for start in range(0, total, chunk):
+        idx = np.arange(start, min(total, start + chunk), dtype=np.int64)
+        s = (idx[:, None] // place[None, :]) % q
+        energy = (s[:, edges[:, 0]] == s[:, edges[:, 1]]).astype(np.float64) @ J
         a = beta * energy
         m = a.max()
         parts.append(m + np.log(np.exp(a - m).sum()))

@@ -6,7 +6,7 @@ import pytest
 
 from oracle import dmtree
 from paper_2406_09769_gb300 import binding as B
-from workloads import ising
+from workloads import ising, potts
 
 pytestmark = pytest.mark.gpu
 
@@ -69,6 +69,25 @@ def _oracle_and_resolution(w, chi):
 def test_tf32_matches_oracle(ctx, Lx, Ly, beta, cp, chi):
     ws = [ising.lattice2d(Lx, Ly, beta, cp, seed=500 * Lx + Ly + i) for i in range(6)]
     logz, status = _run(ctx, ws, chi, B.TN_PREC_TF32)
+    assert list(status) == [0] * len(ws)
+    for i, w in enumerate(ws):
+        ref, resolvable = _oracle_and_resolution(w, chi)
+        tol = RTOL_MIXED if resolvable else RTOL_BELOW_RESOLUTION
+        assert abs(logz[i] - ref) <= tol * abs(ref), (i, logz[i], ref, resolvable)
+
+
+@pytest.mark.parametrize("q,Lx,Ly,chi", [(3, 6, 6, 12), (3, 5, 7, 20), (4, 4, 5, 16)])
+def test_tf32_potts_matches_oracle(ctx, q, Lx, Ly, chi):
+    """Bond dimension q != 2 (q-state Potts): every row takes the general
+    fusion kernel, and contraction shapes that are not multiples of four take
+    the plain-FMA fallback."""
+    ws = [potts.lattice2d(Lx, Ly, 0.6, q, "uniform", seed=300 + 10 * q + i) for i in range(3)]
+    plans = [B.tn_plan(w["n"], w["edges"], np.full(len(w["edges"]), q), chi, env_size=w["Ly"])
+             for w in ws]
+    bufs = [torch.from_numpy(B.pack_sites(p, w["tensors"])).cuda() for p, w in zip(plans, ws)]
+    B.tn_contract_approx(ctx, plans, [b.data_ptr() for b in bufs], B.TN_PREC_TF32, 0,
+                         torch.cuda.current_stream().cuda_stream)
+    logz, status = B.tn_logz(ctx, len(plans))
     assert list(status) == [0] * len(ws)
     for i, w in enumerate(ws):
         ref, resolvable = _oracle_and_resolution(w, chi)

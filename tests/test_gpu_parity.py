@@ -10,7 +10,7 @@ import pytest
 
 from oracle import dmtree
 from paper_2406_09769_gb300 import binding as B
-from workloads import ising, prng
+from workloads import ising, potts, prng
 
 pytestmark = pytest.mark.gpu
 
@@ -199,6 +199,22 @@ def test_contract_matches_oracle(ctx, Lx, Ly, beta, cp, chi):
     ws = [ising.lattice2d(Lx, Ly, beta, cp, seed=1000 * Lx + Ly + i) for i in range(5)]
     logz, status = _run(ctx, ws, chi)
     assert list(status) == [0] * 5
+    for i, w in enumerate(ws):
+        ref = dmtree.partitioned_contract_rows(w, chi)["logz"]
+        assert abs(logz[i] - ref) <= RTOL_LOGZ * abs(ref), (i, logz[i], ref)
+
+
+@pytest.mark.parametrize("q,Lx,Ly,chi", [(3, 6, 6, 12), (3, 5, 7, 20), (4, 4, 5, 16)])
+def test_potts_contract_matches_oracle(ctx, q, Lx, Ly, chi):
+    """Bond dimension q != 2 (q-state Potts): the general fusion and the
+    contraction shapes that are not multiples of four."""
+    ws = [potts.lattice2d(Lx, Ly, 0.6, q, "uniform", seed=300 + 10 * q + i) for i in range(3)]
+    plans = [B.tn_plan(w["n"], w["edges"], np.full(len(w["edges"]), q), chi, env_size=w["Ly"])
+             for w in ws]
+    bufs = [torch.from_numpy(B.pack_sites(p, w["tensors"])).cuda() for p, w in zip(plans, ws)]
+    B.tn_contract_approx(ctx, plans, [b.data_ptr() for b in bufs], B.TN_PREC_FP64, 0, _stream())
+    logz, status = B.tn_logz(ctx, len(plans))
+    assert list(status) == [0] * len(ws)
     for i, w in enumerate(ws):
         ref = dmtree.partitioned_contract_rows(w, chi)["logz"]
         assert abs(logz[i] - ref) <= RTOL_LOGZ * abs(ref), (i, logz[i], ref)
