@@ -388,7 +388,7 @@ __device__ __forceinline__ T quad_sum(T v) {
 // FP32 Householder tridiagonalisation with the matrix in registers: thread
 // (row ri = tid & 127, column half h = tid >> 7) holds A[ri][64 h .. 64 h + 63]
 // (zero outside n x n).  Step k: the owners of row k publish it (= column k)
-// to X, four float4 stores per owner and nothing else, so the next step waits
+// to X, sixteen float4 stores per owner and nothing else, so the next step waits
 // on no serial arithmetic; each of the first four warps sums the squares of
 // the row's tail itself (one float4 per lane and a warp reduction) and forms
 // the reflector (same arithmetic, same values in each), and threads c < 128
