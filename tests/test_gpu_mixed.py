@@ -26,6 +26,19 @@ def ctx():
     return B.tn_ctx_create(0)
 
 
+def _exact_config2(n_inst):
+    """Kac-Ward ln Z of config-2 instances 0..n_inst-1 (tests/golden/exact_logz.txt)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "exact_logz.txt")
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("config2_32x32_gauss_i"):
+                parts = line.split()
+                vals[int(parts[0].rsplit("_i", 1)[1])] = float(parts[-1])
+    return np.array([vals[i] for i in range(n_inst)])
+
+
 def _run(ctx, ws, chi, precision):
     plans = [B.tn_plan(w["n"], w["edges"], np.full(len(w["edges"]), 2), chi, env_size=w["Ly"])
              for w in ws]
@@ -106,6 +119,10 @@ def test_tf32_full_size_config2_sampled(ctx, chi):
     for i in (0, n_inst - 1):
         ref = dmtree.partitioned_contract_rows(ws[i], chi)["logz"]
         assert abs(logz[i] - ref) <= RTOL_MIXED * abs(ref), (i, logz[i], ref)
+    # every instance against the exact (Kac-Ward) value, which the method
+    # reaches at this temperature to FP64 rounding
+    ex = _exact_config2(n_inst)
+    assert np.max(np.abs(logz - ex) / np.abs(ex)) <= RTOL_MIXED
 
 
 def test_tf32_nonfinite_instance_is_isolated(ctx):

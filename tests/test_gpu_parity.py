@@ -45,6 +45,19 @@ def _run(ctx, workloads, chi, precision=B.TN_PREC_FP64):
     return B.tn_logz(ctx, len(plans))
 
 
+def _exact_config2(n_inst):
+    """Kac-Ward ln Z of config-2 instances 0..n_inst-1 (tests/golden/exact_logz.txt)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "exact_logz.txt")
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("config2_32x32_gauss_i"):
+                parts = line.split()
+                vals[int(parts[0].rsplit("_i", 1)[1])] = float(parts[-1])
+    return np.array([vals[i] for i in range(n_inst)])
+
+
 # ------------------------------------------------------------ one DM pass
 
 def _random_chain(seed, d, D):
@@ -221,7 +234,9 @@ def test_potts_contract_matches_oracle(ctx, q, Lx, Ly, chi):
 
 
 def test_full_size_config2_sampled(ctx):
-    """32x32 spin glass, chi = 64, in a batch; instances 0 and last sampled."""
+    """32x32 spin glass, chi = 64, in a batch; instances 0 and last against the
+    oracle, every instance against the exact (Kac-Ward) value, which the method
+    reaches at this temperature to FP64 rounding."""
     n_inst = 8
     ws = [ising.config2_instance(i) for i in range(n_inst)]
     logz, status = _run(ctx, ws, 64)
@@ -229,6 +244,8 @@ def test_full_size_config2_sampled(ctx):
     for i in (0, n_inst - 1):
         ref = dmtree.partitioned_contract_rows(ws[i], 64)["logz"]
         assert abs(logz[i] - ref) <= RTOL_LOGZ * abs(ref), (i, logz[i], ref)
+    ex = _exact_config2(n_inst)
+    assert np.max(np.abs(logz - ex) / np.abs(ex)) <= RTOL_LOGZ
 
 
 def test_nonfinite_instance_is_isolated(ctx):

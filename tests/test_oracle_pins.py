@@ -68,10 +68,26 @@ def test_closed_forms():
         exact.ising_logz_tree(w["J"], 0.7), rel=1e-14)
 
 
+def test_kac_ward_equals_bruteforce_and_transfer_matrix():
+    for (Lx, Ly, beta, cp, seed) in [(3, 3, 0.7, "gauss", 1), (3, 4, 1.1, "pm1", 2),
+                                     (4, 4, 0.44, "ferro", 0), (2, 6, 2.0, "gauss", 4)]:
+        w = ising.lattice2d(Lx, Ly, beta, cp, seed=seed)
+        assert exact.ising_logz_kac_ward(Lx, Ly, w["edges"], w["J"], beta) == pytest.approx(
+            exact.ising_logz_bruteforce(w["n"], w["edges"], w["J"], beta), rel=1e-13)
+    w = ising.lattice2d(8, 10, 0.8, "gauss", seed=9)
+    assert exact.ising_logz_kac_ward(8, 10, w["edges"], w["J"], 0.8) == pytest.approx(
+        exact.ising_logz_transfer_matrix(8, 10, w["edges"], w["J"], 0.8), rel=1e-13)
+
+
 def test_golden_values_reproduce():
     for name, Lx, Ly, beta, cp, seed, method, z in _golden():
+        if method == "kw" and not name.endswith("_i0"):
+            continue  # one 32 x 32 determinant is enough here
         w = ising.lattice2d(Lx, Ly, beta, cp, seed=seed)
-        val = exact.ising_logz_transfer_matrix(Lx, Ly, w["edges"], w["J"], beta)
+        if method == "kw":
+            val = exact.ising_logz_kac_ward(Lx, Ly, w["edges"], w["J"], beta)
+        else:
+            val = exact.ising_logz_transfer_matrix(Lx, Ly, w["edges"], w["J"], beta)
         assert val == pytest.approx(z, rel=1e-13), name
     assert _golden()[0][-1] == pytest.approx(31.564145959482058, rel=1e-15)
 
@@ -87,6 +103,18 @@ def test_dm_is_exact_at_or_above_exact_rank(name):
     chi = 2 ** (Ly // 2)          # maximal bond rank of an MPS over Ly legs of dim 2
     got = dmtree.partitioned_contract_rows(w, chi)["logz"]
     assert abs(got - z) <= 1e-12 * abs(z)
+
+
+@pytest.mark.parametrize("i", [0, 7])
+def test_oracle_full_size_config2_matches_exact(i):
+    """32 x 32 Gaussian spin glass at beta = 0.5, chi = 64: the oracle against the
+    Kac-Ward value.  At this temperature the truncation error is below FP64
+    rounding (measured <= 2.6e-13 relative over instances 0..7)."""
+    row = [r for r in _golden() if r[0] == f"config2_32x32_gauss_i{i}"][0]
+    _, Lx, Ly, beta, cp, seed, _, z = row
+    w = ising.config2_instance(i)
+    got = dmtree.partitioned_contract_rows(w, 64)["logz"]
+    assert abs(got - z) <= 1e-11 * abs(z)
 
 
 def test_config1_exact_at_chi16():
