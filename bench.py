@@ -183,6 +183,19 @@ print(json.dumps({{"instances": i, "seconds": time.perf_counter() - t0, "logz": 
 """
 
 
+def exact_logz_32(n):
+    """Exact (Kac-Ward) ln Z of the first n 32x32 instances of this workload, as
+    stored in tests/golden/exact_logz.txt by tests/golden/make_golden.py."""
+    vals = {}
+    with open(os.path.join(ROOT, "tests", "golden", "exact_logz.txt")) as f:
+        for line in f:
+            if line.startswith("config2_32x32_gauss_i"):
+                parts = line.split()
+                vals[int(parts[0].rsplit("_i", 1)[1])] = float(parts[-1])
+    n = min(n, len(vals))
+    return np.array([vals[i] for i in range(n)])
+
+
 def run_oracle(first, size, chi, seconds, min_inst=1, max_inst=10**6):
     cores = os.cpu_count() or 1
     env = dict(os.environ)
@@ -400,6 +413,11 @@ def bench_ours(args):
                       f"({d['seconds']:.1f} s, FP64 numpy oracle, BLAS threads = cores)"}
         out["parity"] = {"instances": len(ref),
                          "max_rel_logz_err_vs_oracle": float(np.max(np.abs(got - ref) / np.abs(ref)))}
+        if args.size == 32:
+            ex = exact_logz_32(len(logz))
+            out["parity"]["exact_instances"] = len(ex)
+            out["parity"]["max_rel_logz_err_vs_exact"] = float(
+                np.max(np.abs(logz[:len(ex)] - ex) / np.abs(ex)))
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
