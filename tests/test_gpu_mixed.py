@@ -6,7 +6,7 @@ import pytest
 
 from oracle import dmtree
 from paper_2406_09769_gb300 import binding as B
-from workloads import ising, potts
+from workloads import ising, potts, random_tn
 
 pytestmark = pytest.mark.gpu
 
@@ -101,6 +101,19 @@ def test_tf32_potts_matches_oracle(ctx, q, Lx, Ly, chi):
     B.tn_contract_approx(ctx, plans, [b.data_ptr() for b in bufs], B.TN_PREC_TF32, 0,
                          torch.cuda.current_stream().cuda_stream)
     logz, status = B.tn_logz(ctx, len(plans))
+    assert list(status) == [0] * len(ws)
+    for i, w in enumerate(ws):
+        ref, resolvable = _oracle_and_resolution(w, chi)
+        tol = RTOL_MIXED if resolvable else RTOL_BELOW_RESOLUTION
+        assert abs(logz[i] - ref) <= tol * abs(ref), (i, logz[i], ref, resolvable)
+
+
+@pytest.mark.parametrize("L,alpha,chi", [(8, 0.0, 8), (28, 0.0, 32)])
+def test_tf32_random_tensors_match_oracle(ctx, L, alpha, chi):
+    """Random tensor networks with entries uniform on [0, 1], including the
+    paper's 28 x 28 lattice size."""
+    ws = [random_tn.lattice2d(L, L, alpha, seed=900 + 7 * L + i) for i in range(3)]
+    logz, status = _run(ctx, ws, chi, B.TN_PREC_TF32)
     assert list(status) == [0] * len(ws)
     for i, w in enumerate(ws):
         ref, resolvable = _oracle_and_resolution(w, chi)

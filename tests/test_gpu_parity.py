@@ -10,7 +10,7 @@ import pytest
 
 from oracle import dmtree
 from paper_2406_09769_gb300 import binding as B
-from workloads import ising, potts, prng
+from workloads import ising, potts, prng, random_tn
 
 pytestmark = pytest.mark.gpu
 
@@ -231,6 +231,23 @@ def test_potts_contract_matches_oracle(ctx, q, Lx, Ly, chi):
     for i, w in enumerate(ws):
         ref = dmtree.partitioned_contract_rows(w, chi)["logz"]
         assert abs(logz[i] - ref) <= RTOL_LOGZ * abs(ref), (i, logz[i], ref)
+
+
+@pytest.mark.parametrize("L,alpha,chi", [(8, 0.0, 8), (8, -0.3, 8), (28, -0.2, 32)])
+def test_random_tensors_match_oracle(ctx, L, alpha, chi):
+    """Random tensor networks (entries uniform on [alpha, 1]), including the
+    paper's 28 x 28 lattice size.  With negative entries Z itself can be
+    negative (8 x 8, alpha = -0.3, seed 957): ln Z is then undefined, the oracle
+    returns sign -1 and the library must report TN_ERR_NONPOSITIVE (5)."""
+    ws = [random_tn.lattice2d(L, L, alpha, seed=900 + 7 * L + i) for i in range(3)]
+    logz, status = _run(ctx, ws, chi)
+    for i, w in enumerate(ws):
+        r = dmtree.partitioned_contract_rows(w, chi)
+        if r["sign"] < 0:
+            assert status[i] == 5, (i, status[i])
+            continue
+        assert status[i] == 0, (i, status[i])
+        assert abs(logz[i] - r["logz"]) <= RTOL_LOGZ * abs(r["logz"]), (i, logz[i], r["logz"])
 
 
 def test_full_size_config2_sampled(ctx):
