@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 from paper_2406_09769_gb300 import binding as B
-from workloads import ising
+from workloads import ising, potts
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -51,17 +51,18 @@ def test_plan_counts_and_offsets():
     assert [p.site_offset(v) for v in range(36)] == list(np.cumsum([0] + sizes[:-1]))
 
 
-def _expected_flops(Lx, Ly, chi):
+def _expected_flops(Lx, Ly, chi, q=2):
     """Sec. 2.2 cost model over the shapes the row-partition method produces,
-    written independently of the planner (2 flops per multiply-add)."""
-    d = [2] * Ly
-    bond = [2] * (Ly - 1)            # boundary MPS after row 0 (horizontal bonds)
+    written independently of the planner (2 flops per multiply-add); every bond
+    of dimension q."""
+    d = [q] * Ly
+    bond = [q] * (Ly - 1)            # boundary MPS after row 0 (horizontal bonds)
     env = local = dens = proj = 0.0
     for _ in range(Lx - 2):
-        D = [b * 2 for b in bond] + [1]
+        D = [b * q for b in bond] + [1]
         r = [d[0]]
         for k in range(1, Ly - 1):
-            r.append(min(chi, r[-1] * d[k], D[k], 2 ** (Ly - 1 - k)))
+            r.append(min(chi, r[-1] * d[k], D[k], q ** (Ly - 1 - k)))
         for k in range(Ly - 1, 1, -1):
             env += 2.0 * D[k - 1] * d[k] * D[k] * D[k] + 2.0 * D[k - 1] ** 2 * d[k] * D[k]
         for k in range(1, Ly - 1):
@@ -83,6 +84,22 @@ def test_plan_flops_match_cost_model(Lx, Ly, chi):
     assert info["flops_local"] == pytest.approx(local)
     assert info["flops_density"] == pytest.approx(dens)
     assert info["flops_project"] == pytest.approx(proj)
+
+
+@pytest.mark.parametrize("Lx,Ly,chi,q", [(6, 6, 12, 3), (5, 7, 20, 3), (4, 5, 16, 4)])
+def test_plan_with_bond_dimension_q(Lx, Ly, chi, q):
+    """Potts networks: site buffer of q^degree entries per vertex and the cost
+    model with every bond of dimension q."""
+    w = potts.lattice2d(Lx, Ly, 0.6, q)
+    p = B.tn_plan(w["n"], w["edges"], np.full(len(w["edges"]), q), chi, env_size=Ly)
+    sizes = [t.size for t in w["tensors"]]
+    assert p.info["site_elems"] == sum(sizes)
+    assert [p.site_offset(v) for v in range(w["n"])] == list(np.cumsum([0] + sizes[:-1]))
+    env, local, dens, proj = _expected_flops(Lx, Ly, chi, q)
+    assert p.info["flops_env"] == pytest.approx(env)
+    assert p.info["flops_local"] == pytest.approx(local)
+    assert p.info["flops_density"] == pytest.approx(dens)
+    assert p.info["flops_project"] == pytest.approx(proj)
 
 
 def test_plan_rejects_malformed_input():
