@@ -49,7 +49,8 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="tf32", choices=["fp64", "tf32", "tf32fast", "bf16"])
+    p.add_argument("--precision", default="tf32",
+                   choices=["fp64", "tf32", "tf32fast", "tf32gram", "bf16"])
     p.add_argument("--chi", type=int, default=64)
     p.add_argument("--size", type=int, default=32)
     p.add_argument("--batch", type=int, default=304)
@@ -262,7 +263,7 @@ def bench_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     prec = {"fp64": B.TN_PREC_FP64, "tf32": B.TN_PREC_TF32, "tf32fast": B.TN_PREC_TF32_FAST,
-            "bf16": B.TN_PREC_BF16}[args.precision]
+            "tf32gram": B.TN_PREC_TF32_GRAM, "bf16": B.TN_PREC_BF16}[args.precision]
     Bn, K, W = args.batch, args.steps, args.warmup
 
     first, _ = rank_slice(rank, Bn)
@@ -354,7 +355,7 @@ def bench_ours(args):
         bound, peak, note = "alu", FP32_ALU_TFLOPS, "FP32 152 SMs x 128 lanes x 2 x 2.07 GHz"
     else:
         bf16 = pk.get("bf16_tflops_sustained", FALLBACK["bf16_tflops_sustained"])
-        is_tf32 = prec in (B.TN_PREC_TF32, B.TN_PREC_TF32_FAST)
+        is_tf32 = prec in (B.TN_PREC_TF32, B.TN_PREC_TF32_FAST, B.TN_PREC_TF32_GRAM)
         peak = bf16 * (TF32_PER_BF16 if is_tf32 else 1.0)
         bound, note = "tensor", f"{pk_src} bf16 sustained" + (" x 1.1/2.25 (tf32)" if is_tf32 else "")
     # DRAM bytes per launch of the dominant kernel from an ncu capture; null when
@@ -393,7 +394,8 @@ def bench_ours(args):
         "metric": "approx contractions/s", "value": value, "unit": "contractions/s",
         "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": total_ms / K,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "f64", "tf32": "tf32", "tf32fast": "tf32", "bf16": "bf16"}[args.precision],
+        "dtype": {"fp64": "f64", "tf32": "tf32", "tf32fast": "tf32", "tf32gram": "tf32",
+                  "bf16": "bf16"}[args.precision],
         "data": "synthetic (seeded instances)",
         "config": {"workload": WORKLOAD, "size": args.size, "chi": args.chi, "batch": Bn,
                    "precision": args.precision, "l2": "flushed between steps (256 MB write)",

@@ -49,15 +49,30 @@ typedef enum {
  *   TN_PREC_FP64:      every contraction, eigensolver and scale in FP64.
  *   TN_PREC_TF32:      FP32 storage; every contraction on tcgen05 tensor cores
  *                      as a compensated 3-term TF32 split (hi*hi + hi*lo +
- *                      lo*hi, FP32 accumulation, ~FP32 accuracy); FP32
- *                      eigensolver; root norm, log-scale and the closing
- *                      contraction in FP64.
- *   TN_PREC_TF32_FAST: as TN_PREC_TF32 but the density-matrix side (memoised
- *                      environments, L_v) in plain TF32; only the value path
- *                      (local blocks, projections) is compensated.  Loses
- *                      eigen-directions below ~1e-3 of the largest eigenvalue.
+ *                      lo*hi, FP32 accumulation, ~FP32 accuracy).  The density
+ *                      matrix L_v = M_v R_v M_v^T is never formed: R_v = C_v
+ *                      C_v^T (FP32 Cholesky), K_v = M_v C_v, and the leading
+ *                      eigenvectors of L_v are the leading left singular
+ *                      vectors of K_v (FP32 bidiagonal SVD), so L_v's spectrum
+ *                      is resolved to ~eps_32^2 of its largest eigenvalue, as
+ *                      an FP64 density matrix would be.  Root norm, log-scale
+ *                      and the closing contraction in FP64.
+ *   TN_PREC_TF32_FAST: L_v formed explicitly in plain TF32 (memoised
+ *                      environments too) and an FP32 eigensolver; only the
+ *                      value path (local blocks, projections) is compensated.
+ *                      Loses eigen-directions below ~1e-3 of the largest
+ *                      eigenvalue.
+ *   TN_PREC_TF32_GRAM: as TN_PREC_TF32_FAST with every contraction
+ *                      compensated: L_v in FP32 resolves eigen-directions only
+ *                      down to ~1e-7 of its largest eigenvalue.
  *   TN_PREC_BF16:      reserved; returns TN_ERR_UNSUPPORTED in this build.  */
-enum { TN_PREC_FP64 = 0, TN_PREC_BF16 = 1, TN_PREC_TF32 = 2, TN_PREC_TF32_FAST = 3 };
+enum {
+  TN_PREC_FP64 = 0,
+  TN_PREC_BF16 = 1,
+  TN_PREC_TF32 = 2,
+  TN_PREC_TF32_FAST = 3,
+  TN_PREC_TF32_GRAM = 4
+};
 
 /* The tensor network graph G = (V, E) of Sec. 2.1.  Host memory, caller-owned.
  * edge_v[e] == -1 marks an open (uncontracted) edge; this build requires a
@@ -303,7 +318,8 @@ enum {
   TN_KC_PROJECT = 6,  /* projector application U_v^T M_v                     */
   TN_KC_ROOT = 7,     /* root M_r and its normalisation                      */
   TN_KC_CLOSE = 8,    /* closing contraction of the last partition           */
-  TN_KC_COUNT = 9
+  TN_KC_FACTOR = 9,   /* Cholesky factors of the memoised environments       */
+  TN_KC_COUNT = 10
 };
 /* Turn per-launch CUDA-event timing on (1) or off (0) for later batches of
  * ctx.  Launch counting is always on.  Timing adds two events per launch,

@@ -18,7 +18,7 @@ TN_OK = 0
 STATUS_NAMES = {0: "TN_OK", 1: "TN_ERR_INVALID", 2: "TN_ERR_OOM", 3: "TN_ERR_CUDA",
                 4: "TN_ERR_NONFINITE", 5: "TN_ERR_NONPOSITIVE", 6: "TN_ERR_TIMEOUT",
                 7: "TN_ERR_EIG_NOCONV", 8: "TN_ERR_UNSUPPORTED"}
-TN_PREC_FP64, TN_PREC_BF16, TN_PREC_TF32, TN_PREC_TF32_FAST = 0, 1, 2, 3
+TN_PREC_FP64, TN_PREC_BF16, TN_PREC_TF32, TN_PREC_TF32_FAST, TN_PREC_TF32_GRAM = 0, 1, 2, 3, 4
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _vp = ctypes.c_void_p
@@ -60,7 +60,8 @@ EXPORTS = ("tn_plan", "tn_plan_destroy", "tn_plan_query", "tn_plan_site_offset",
            "tn_rank_model_grad", "tn_rank_model_train",
            "tn_ctx_set_profiling", "tn_ctx_profile", "tn_last_error")
 
-KERNEL_CLASSES = ("norm", "fuse", "env", "local", "density", "eig", "project", "root", "close")
+KERNEL_CLASSES = ("norm", "fuse", "env", "local", "density", "eig", "project", "root", "close",
+                  "factor")
 
 
 def lib():

@@ -265,7 +265,8 @@ void* pinned_get(tn_ctx* c, size_t bytes) {
 struct StepTables {
   tn::FuseSite* fuse;
   int64_t* y_off;
-  int32_t* D;  // n + 1 entries (last = max D)
+  int32_t* D;      // n + 1 entries (last = max D)
+  int64_t* r_off;  // memoised density matrix R_k offsets (n entries)
 };
 
 std::vector<StepTables> upload_tables(tn_ctx* c, const tn_plan_t* P, const std::vector<Lay>& lay,
@@ -279,7 +280,7 @@ std::vector<StepTables> upload_tables(tn_ctx* c, const tn_plan_t* P, const std::
   for (size_t s = 0; s < P->steps.size(); ++s) {
     so[s] = tot;
     const int n = P->steps[s].n;
-    tot += align256(sizeof(tn::FuseSite) * n) + align256(sizeof(int64_t) * n) +
+    tot += align256(sizeof(tn::FuseSite) * n) + 2 * align256(sizeof(int64_t) * n) +
            align256(sizeof(int32_t) * (n + 1));
   }
   char* h = static_cast<char*>(pinned_get(c, tot));
@@ -319,6 +320,11 @@ std::vector<StepTables> upload_tables(tn_ctx* c, const tn_plan_t* P, const std::
     D.push_back(mx);
     std::memcpy(h + q, D.data(), sizeof(int32_t) * (n + 1));
     out[s].D = reinterpret_cast<int32_t*>(dbase + q);
+    q += align256(sizeof(int32_t) * (n + 1));
+    std::vector<int64_t> ro(lay[s].r_off);
+    ro.resize(n, 0);
+    std::memcpy(h + q, ro.data(), sizeof(int64_t) * n);
+    out[s].r_off = reinterpret_cast<int64_t*>(dbase + q);
   }
   ck(cudaMemcpyAsync(dbase, h, tot, cudaMemcpyHostToDevice, st), "upload tables");
   ck(cudaEventRecord(c->pinned_free, st), "cudaEventRecord");
@@ -621,8 +627,11 @@ void tgemm(tn_ctx* c, int cls, const float* A, long long sA, int lda, const floa
 }
 
 // sub_split: compensated products also on the density-matrix side (env, L_v).
+// factored: R_k = C_k C_k^T and the leading left singular vectors of
+// K_v = M_v C_k instead of forming L_v (tab: this step's device tables).
 void dm_pass_tc(tn_ctx* c, const tn::Step& st, const Lay& l, const WsF& w, float* Snext, int B,
-                int sub_split, cudaStream_t strm, const PassCtx* pc = nullptr) {
+                int sub_split, bool factored, const StepTables* tab, cudaStream_t strm,
+                const PassCtx* pc = nullptr) {
   const bool want_lam = pc && (pc->learned || pc->record);
   const int n = st.n;
   const auto& D = st.D;
@@ -642,6 +651,15 @@ void dm_pass_tc(tn_ctx* c, const tn::Step& st, const Lay& l, const WsF& w, float
           nullptr, 0, 0, 0, Dl, Dl, dk * Dr, B, nullptr, 0, w.amax + (k - 1), w.sAmax, sub_split,
           strm);
   }
+  if (factored && n >= 3) {
+    // R_k = C_k C_k^T for every vertex of the pass, C_k^T in place of R_k
+    int maxD = 1;
+    for (int k = 1; k <= n - 2; ++k) maxD = std::max(maxD, D[k]);
+    Scope(c, TN_KC_FACTOR, strm),
+    ck(tn::launch_chol_env(w.R, w.sR, tab->r_off, tab->D, maxD, w.amax, w.sAmax, 1, n - 2, B,
+                           strm),
+       "cholesky launch");
+  }
   for (int k = 1; k <= n - 2; ++k) {
     const int rp = st.r[k - 1], rk = st.r[k], dk = d[k], Dl = D[k - 1], Dr = D[k];
     const int A = rp * dk;
@@ -650,16 +668,27 @@ void dm_pass_tc(tn_ctx* c, const tn::Step& st, const Lay& l, const WsF& w, float
     // M_v = P_{v-1} Y_v (value path, compensated); also M_v^T for the projector.
     tgemm(c, TN_KC_LOCAL, Pp, sPp, Dl, w.Yt + l.y_off[k], w.sY, Dl, w.M, w.sM, dk * Dr, w.Mt,
           w.sM, A, Dr, rp, dk * Dr, Dl, B, nullptr, 0, nullptr, 0, 1, strm);
-    // L_v = M_v R_k M_v^T
-    tgemm(c, TN_KC_DENSITY, w.M, w.sM, Dr, w.R + l.r_off[k], w.sR, Dr, w.G, w.sM, Dr, nullptr, 0, 0,
-          0, A, Dr, Dr, B, w.amax + k, w.sAmax, nullptr, 0, sub_split, strm);
-    tgemm(c, TN_KC_DENSITY, w.G, w.sM, Dr, w.M, w.sM, Dr, w.L, w.sL, A, nullptr, 0, 0, 0, A, A, Dr,
-          B, nullptr, 0, nullptr, 0, sub_split, strm);
     float* Uk = Snext + l.s_off[k];
-    Scope(c, TN_KC_EIG, strm),
-    ck(tn::launch_eigh_top<float>(w.L, w.sL, Uk, w.sS, w.Ut, w.sUt, w.lam, w.sLam, A, rk,
-                                  want_lam ? A : 0, c->status, B, strm),
-       "eigh launch");
+    if (factored) {
+      // K_v = M_v C_k (C_k^T stored row-major: the K-major second operand)
+      tgemm(c, TN_KC_DENSITY, w.M, w.sM, Dr, w.R + l.r_off[k], w.sR, Dr, w.G, w.sM, Dr, nullptr,
+            0, 0, 0, A, Dr, Dr, B, nullptr, 0, nullptr, 0, 1, strm);
+      // U_v = leading left singular vectors of K_v = leading eigenvectors of L_v
+      Scope(c, TN_KC_EIG, strm),
+      ck(tn::launch_svd_left(w.G, w.sM, A, Dr, Uk, w.sS, w.Ut, w.sUt, w.lam, w.sLam, rk,
+                             want_lam ? A : 0, c->status, B, strm),
+         "svd launch");
+    } else {
+      // L_v = M_v R_k M_v^T
+      tgemm(c, TN_KC_DENSITY, w.M, w.sM, Dr, w.R + l.r_off[k], w.sR, Dr, w.G, w.sM, Dr, nullptr,
+            0, 0, 0, A, Dr, Dr, B, w.amax + k, w.sAmax, nullptr, 0, sub_split, strm);
+      tgemm(c, TN_KC_DENSITY, w.G, w.sM, Dr, w.M, w.sM, Dr, w.L, w.sL, A, nullptr, 0, 0, 0, A, A,
+            Dr, B, nullptr, 0, nullptr, 0, sub_split, strm);
+      Scope(c, TN_KC_EIG, strm),
+      ck(tn::launch_eigh_top<float>(w.L, w.sL, Uk, w.sS, w.Ut, w.sUt, w.lam, w.sLam, A, rk,
+                                    want_lam ? A : 0, c->status, B, strm),
+         "eigh launch");
+    }
     rank_hook<float>(c, pc, st, k, A, rk, w.lam, w.sLam, Uk, w.sS, w.Ut, w.sUt, B, strm);
     // P_v = U_v^T M_v (value path, compensated)
     tgemm(c, TN_KC_PROJECT, w.Ut, w.sUt, A, w.Mt, w.sM, A, w.P, w.sP, Dr, nullptr, 0, 0, 0, rk,
@@ -673,7 +702,15 @@ void dm_pass_tc(tn_ctx* c, const tn::Step& st, const Lay& l, const WsF& w, float
 }
 
 void run_plan_tc(tn_ctx* c, const tn_plan_t* P, int B, const double* const* tens_dev,
-                 int sub_split, bool learned, cudaStream_t strm) {
+                 int sub_split, bool factored, bool learned, cudaStream_t strm) {
+  if (factored)
+    for (const tn::Step& st : P->steps) {
+      if (st.kind != 1) continue;
+      for (int k = 1; k <= st.n - 2; ++k)
+        if (!tn::svd_left_supported(st.r[k - 1] * st.d[k], st.D[k], st.r[k]))
+          fail(TN_ERR_UNSUPPORTED,
+               "TN_PREC_TF32 needs dim A_v <= 128, tree-edge dims <= 128 and ranks <= 64");
+    }
   std::vector<Lay> lay;
   for (const tn::Step& st : P->steps) lay.push_back(lay_f32(st));
   ensure_results(c, B);
@@ -719,7 +756,7 @@ void run_plan_tc(tn_ctx* c, const tn_plan_t* P, int B, const double* const* tens
                              strm),
          "fuse");
       const PassCtx pc = learn_pass(ls, c, st);
-      dm_pass_tc(c, st, lay[s], w, Snext, B, sub_split, strm, &pc);
+      dm_pass_tc(c, st, lay[s], w, Snext, B, sub_split, factored, &tabs[s], strm, &pc);
       std::swap(Scur, Snext);
     } else {
       Scope(c, TN_KC_FUSE, strm),
@@ -787,7 +824,8 @@ extern "C" tn_status tn_ctx_create(int32_t device, tn_ctx_t** out) {
     int major = 0, minor = 0;
     ck(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device), "attribute");
     ck(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device), "attribute");
-    c->tc_ready = (major == 10 && minor == 3) && tn::tc_gemm_configure() == cudaSuccess;
+    c->tc_ready = (major == 10 && minor == 3) && tn::tc_gemm_configure() == cudaSuccess &&
+                  tn::svd_configure() == cudaSuccess;
     cudaGetLastError();
   });
   if (s != TN_OK) {
@@ -836,10 +874,11 @@ extern "C" tn_status tn_contract_approx(tn_ctx_t* c, const tn_plan_t* const* pla
     cudaStream_t strm = static_cast<cudaStream_t>(stream);
     if (precision == TN_PREC_FP64) {
       run_plan(c, plans[0], n_inst, sites_dev, precision, learned_chi != 0, strm);
-    } else if (precision == TN_PREC_TF32 || precision == TN_PREC_TF32_FAST) {
+    } else if (precision == TN_PREC_TF32 || precision == TN_PREC_TF32_FAST ||
+               precision == TN_PREC_TF32_GRAM) {
       if (!c->tc_ready) fail(TN_ERR_UNSUPPORTED, "tcgen05 path unavailable on this device");
-      run_plan_tc(c, plans[0], n_inst, sites_dev, precision == TN_PREC_TF32 ? 1 : 0,
-                  learned_chi != 0, strm);
+      run_plan_tc(c, plans[0], n_inst, sites_dev, precision == TN_PREC_TF32_FAST ? 0 : 1,
+                  precision == TN_PREC_TF32, learned_chi != 0, strm);
     } else {
       fail(TN_ERR_UNSUPPORTED, "precision mode not implemented in this build");
     }

@@ -131,6 +131,24 @@ cudaError_t launch_water_fill(const double* spec, const int* cap, const int* pas
 int water_fill_max_edges();
 cudaError_t launch_iota(int* x, int n, cudaStream_t st);
 
+// Factored density matrices (svd.cu).  launch_chol_env: every memoised
+// environment R_k (k = k0 .. k0 + nk - 1, n = D[k] <= 128, at R + i sR +
+// r_off[k], scaled by 1 / amax[i s_amax + k] as float bits) is replaced in
+// place by C^T (row-major) with R_k / amax = C C^T, C lower triangular.
+// launch_svd_left: the r (<= 64) leading left singular vectors of K_i (m x n,
+// row-major, m, n <= 128) into U (m x r) and Ut (r x m, may be NULL), signed
+// so the largest-|.| entry is positive, and sigma_t^2 for t < nlam into lam.
+cudaError_t launch_chol_env(float* R, long long sR, const int64_t* r_off, const int32_t* D,
+                            int maxD, const unsigned int* amax, long long s_amax, int k0, int nk,
+                            int batch, cudaStream_t st);
+cudaError_t launch_svd_left(const float* K, long long sK, int m, int n, float* U, long long sU,
+                            float* Ut, long long sUt, double* lam, long long slam, int r,
+                            int nlam, int* status, int batch, cudaStream_t st);
+bool svd_left_supported(int m, int n, int r);
+size_t svd_left_smem_bytes(int m, int n, int r);
+size_t chol_env_smem_bytes(int n);
+cudaError_t svd_configure();
+
 template <typename T>
 size_t eigh_smem_bytes(int n, int r, int nlam);
 template <typename T>

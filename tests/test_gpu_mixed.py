@@ -1,6 +1,9 @@
 """GPU parity of the mixed-precision (TF32 tensor-core) path against the FP64
 oracle.  Bar: relative ln Z error <= 1e-6 with the same chi (the truncation is
-the oracle's, so this is the error the mixed precision adds beyond it)."""
+the oracle's, so this is the error the mixed precision adds beyond it), on
+every case, including truncations far below the largest eigenvalue: the
+default mixed mode never forms L_v, it takes the leading left singular
+vectors of K_v = M_v C_v with R_v = C_v C_v^T."""
 import numpy as np
 import pytest
 
@@ -55,24 +58,8 @@ def test_tf32_config1_exact(ctx):
     assert abs(logz[0] - 31.564145959482058) <= RTOL_MIXED * 31.6
 
 
-RTOL_BELOW_RESOLUTION = 2e-5
-
-
-def _oracle_and_resolution(w, chi):
-    """ln Z and whether every cut is resolvable in FP32: each truncation is
-    either inactive (first discarded eigenvalue < 1e-14 of the top) or cuts
-    above the FP32 eigensolver's resolution (last kept eigenvalue > 1e-5 of
-    the top).  Cuts between those levels keep directions an FP32 density
-    matrix cannot order (~1e-7 of the top eigenvalue), which costs up to a
-    few 1e-6 relative in ln Z (bound RTOL_BELOW_RESOLUTION, measured)."""
-    trace = []
-    logz = dmtree.partitioned_contract_rows(w, chi, trace=trace)["logz"]
-    for step in trace:
-        for rec in step["vertices"]:
-            lam, r = rec["lam"], rec["r"]
-            if r < len(lam) and lam[r] > 1e-14 * lam[0] and lam[r - 1] < 1e-5 * lam[0]:
-                return logz, False
-    return logz, True
+def _oracle(w, chi):
+    return dmtree.partitioned_contract_rows(w, chi)["logz"]
 
 
 @pytest.mark.parametrize("Lx,Ly,beta,cp,chi", [
@@ -84,9 +71,8 @@ def test_tf32_matches_oracle(ctx, Lx, Ly, beta, cp, chi):
     logz, status = _run(ctx, ws, chi, B.TN_PREC_TF32)
     assert list(status) == [0] * len(ws)
     for i, w in enumerate(ws):
-        ref, resolvable = _oracle_and_resolution(w, chi)
-        tol = RTOL_MIXED if resolvable else RTOL_BELOW_RESOLUTION
-        assert abs(logz[i] - ref) <= tol * abs(ref), (i, logz[i], ref, resolvable)
+        ref = _oracle(w, chi)
+        assert abs(logz[i] - ref) <= RTOL_MIXED * abs(ref), (i, logz[i], ref)
 
 
 @pytest.mark.parametrize("q,Lx,Ly,chi", [(3, 6, 6, 12), (3, 5, 7, 20), (4, 4, 5, 16)])
@@ -103,9 +89,8 @@ def test_tf32_potts_matches_oracle(ctx, q, Lx, Ly, chi):
     logz, status = B.tn_logz(ctx, len(plans))
     assert list(status) == [0] * len(ws)
     for i, w in enumerate(ws):
-        ref, resolvable = _oracle_and_resolution(w, chi)
-        tol = RTOL_MIXED if resolvable else RTOL_BELOW_RESOLUTION
-        assert abs(logz[i] - ref) <= tol * abs(ref), (i, logz[i], ref, resolvable)
+        ref = _oracle(w, chi)
+        assert abs(logz[i] - ref) <= RTOL_MIXED * abs(ref), (i, logz[i], ref)
 
 
 @pytest.mark.parametrize("L,alpha,chi", [(8, 0.0, 8), (28, 0.0, 32)])
@@ -116,9 +101,8 @@ def test_tf32_random_tensors_match_oracle(ctx, L, alpha, chi):
     logz, status = _run(ctx, ws, chi, B.TN_PREC_TF32)
     assert list(status) == [0] * len(ws)
     for i, w in enumerate(ws):
-        ref, resolvable = _oracle_and_resolution(w, chi)
-        tol = RTOL_MIXED if resolvable else RTOL_BELOW_RESOLUTION
-        assert abs(logz[i] - ref) <= tol * abs(ref), (i, logz[i], ref, resolvable)
+        ref = _oracle(w, chi)
+        assert abs(logz[i] - ref) <= RTOL_MIXED * abs(ref), (i, logz[i], ref)
 
 
 @pytest.mark.parametrize("chi", [32, 64])
@@ -153,12 +137,26 @@ def test_tf32_nonfinite_instance_is_isolated(ctx):
 def test_tf32_fast_mode_error_is_bounded(ctx):
     """Plain TF32 on the density-matrix side: directions below ~1e-3 of the
     top eigenvalue are resolved only to TF32 noise; the measured cost on the
-    32x32 chi=64 workload is a few 1e-6 relative in ln Z (bound 2e-5 here)."""
+    32x32 chi=64 workload is a few 1e-6 relative in ln Z (bound 2e-5 here).
+    A fast mode with a stated error, not the default."""
     ws = [ising.config2_instance(i) for i in range(4)]
     fast, st = _run(ctx, ws, 64, B.TN_PREC_TF32_FAST)
     fp64, st64 = _run(ctx, ws, 64, B.TN_PREC_FP64)
     assert list(st) == [0] * 4 and list(st64) == [0] * 4
     assert np.max(np.abs(fast - fp64) / np.abs(fp64)) <= 2e-5
+
+
+def test_tf32_gram_mode_error_is_bounded(ctx):
+    """L_v formed in FP32 (compensated products) with an FP32 eigensolver:
+    eigen-directions below ~1e-7 of the top eigenvalue are noise.  On the
+    32x32 chi=64 workload the cost stays below 1e-6 relative; on strongly
+    truncated runs it reaches a few 1e-6 (measured), which is why it is not
+    the default."""
+    ws = [ising.config2_instance(i) for i in range(4)]
+    gram, st = _run(ctx, ws, 64, B.TN_PREC_TF32_GRAM)
+    fp64, st64 = _run(ctx, ws, 64, B.TN_PREC_FP64)
+    assert list(st) == [0] * 4 and list(st64) == [0] * 4
+    assert np.max(np.abs(gram - fp64) / np.abs(fp64)) <= 1e-6
 
 
 def test_unsupported_precision_is_reported(ctx):
