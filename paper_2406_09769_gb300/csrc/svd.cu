@@ -123,82 +123,154 @@ __global__ void __launch_bounds__(kThreads) k_chol_env(float* __restrict__ R, lo
 }
 
 // ---------------------------------------------------------------- SVD
-// Shared layout (floats): a region of max(m * ldk, r * zld) holding K during
-// the bidiagonalisation and the Golub-Kahan vectors afterwards; the packed
-// left reflectors (row k + 1 .. m - 1 of reflector k, back to back); then
-// the 128/256-entry work vectors.
-struct SvdLayout {
-  int ldk, N, zld, region, refl;
-};
+// Bidiagonalisation layout: a 16 x 16 thread grid, thread (a = 2 warp + lane /
+// 16, b = lane % 16) holds the 8 x 8 tile K[8a .. 8a+7][8b .. 8b+7] in
+// registers (zero outside m x n).  Step k needs column k (left reflector) and
+// row k (right reflector): their owners publish them to shared memory at the
+// end of step k - 1.  Every warp forms the reflector scalars itself from the
+// published vectors (same arithmetic, same values in each), so a step has two
+// barriers: one after the per-warp column sums u^T K, one after the update.
+//   column sums  w = tau K^T u : FMAs on the tile, the warp's two tile rows
+//                combined by a shuffle, the eight warps' partials summed by
+//                every reader from shared memory;
+//   row sums     K v          : FMAs on the tile, summed over the sixteen
+//                lanes of a tile row by a butterfly (bitwise the same in
+//                every lane);
+//   update       K -= u w^T + z v^T with z = tau' (K v - u (w . v)), all in
+//                registers (u, z zero outside rows k+1 .. m-1, w, v outside
+//                columns k+1 .. n-1, so the whole tile updates unmasked).
+// Vectors phase: thread quad (column col = tid / 4, quarter qr = tid % 4)
+// holds rows 32 qr .. 32 qr + 31 of its vector; shared vectors use padded
+// rows (row c at c + 4 (c / 32)), so the quad's float4 reads hit disjoint bank
+// groups.  Left reflector k is kept from row 4 floor(k / 4) to mr - 1 (mr = m
+// rounded up to 4) in padded coordinates, back to back.
+constexpr int kRld = 144;
+__host__ __device__ __forceinline__ int rpad(int c) { return c + (c >> 5) * 4; }
 
-__host__ __device__ inline SvdLayout svd_layout(int m, int n, int r) {
-  SvdLayout L;
-  L.ldk = n | 1;
-  const int p = m < n ? m : n;
-  L.N = (m < n) ? 2 * p + 1 : 2 * p;
-  L.zld = L.N + 1;
-  const int a = m * L.ldk, z = r * L.zld;
-  L.region = ((a > z ? a : z) + 3) & ~3;
-  L.refl = ((p * (m - 1) - (p * (p - 1)) / 2) + 3) & ~3;
-  if (L.refl < 4) L.refl = 4;
-  return L;
+__host__ __device__ inline int refl_len(int k, int m) {
+  const int mr = (m + 3) & ~3;
+  return rpad(mr) - rpad(k & ~3);
 }
 
-constexpr int kSmallFloats = 128 * 8 + 256 * 3 + 2 * 132 + 64 + 16;
+__host__ __device__ inline int refl_total(int m, int p) {
+  int t = 0;
+  for (int k = 0; k < p; ++k) t += refl_len(k, m);
+  return t;
+}
 
-__host__ __device__ inline int refl_off(int k, int m) { return k * (m - 1) - (k * (k - 1)) / 2; }
+// floats after the reflectors and the Golub-Kahan vectors
+constexpr int kSmallFloats = 256 + 256 + 1024 + 4 * 128 + 3 * 256 + 2 * kRld + 64 + 16 + 132 + 128;
 
+// Sturm count of T_GK - x I (zero diagonal; eigenvalues below x).  The
+// recurrence q_0 = -x, q_j = -x - g_{j-1}^2 / q_{j-1} is taken two entries
+// at a time: with t = x q + g^2, the odd entry is q' = -t / q (only its sign
+// is needed, and q' < 0 exactly when t and q have the same sign) and the next
+// even entry is q'' = -x + g'^2 q / t, one division per pair.  Pivots below
+// pivmin in magnitude count as -pivmin, as in the plain recurrence.
 __device__ int sturm_gk(const float* e2, int N, float x, float pivmin) {
-  // T_GK has a zero diagonal: q_0 = -x, q_j = -x - g_{j-1}^2 / q_{j-1}
   float q = -x;
   if (fabsf(q) < pivmin) q = -pivmin;
   int c = (q < 0.f);
-  for (int j = 1; j < N; ++j) {
-    q = -x - __fdividef(e2[j - 1], q);
-    if (fabsf(q) < pivmin) q = -pivmin;
-    c += (q < 0.f);
+  int j = 1;
+  for (; j + 1 < N; j += 2) {
+    const float t = fmaf(x, q, e2[j - 1]);
+    float qn;
+    if (fabsf(t) < pivmin * fabsf(q)) {  // q' = -pivmin
+      c += 1;
+      qn = fmaf(e2[j], __fdividef(1.f, pivmin), -x);
+    } else {
+      c += ((t > 0.f) == (q > 0.f));
+      qn = fmaf(e2[j], __fdividef(q, t), -x);
+    }
+    if (fabsf(qn) < pivmin) qn = -pivmin;
+    c += (qn < 0.f);
+    q = qn;
+  }
+  if (j < N) {  // a last odd entry
+    const float t = fmaf(x, q, e2[j - 1]);
+    c += (fabsf(t) < pivmin * fabsf(q)) ? 1 : ((t > 0.f) == (q > 0.f));
   }
   return c;
 }
 
-__global__ void __launch_bounds__(kThreads) k_svd_left(const float* __restrict__ Kg, long long sK,
-                                                        int m, int n, float* __restrict__ Ug,
-                                                        long long sU, float* __restrict__ Utg,
-                                                        long long sUt, double* __restrict__ lamg,
-                                                        long long slam, int r, int nlam,
-                                                        int* __restrict__ status) {
+// Householder reflector for x = (alpha, tail) with s = |tail|^2: returns
+// beta (the new leading entry), tau and the tail scale sc (u = (1, sc tail)).
+// tau = 2 / (u^T u) = 2 / (1 + s sc^2) keeps H = I - tau u u^T orthogonal to
+// working precision whatever the rounding of beta and sc.
+__device__ __forceinline__ void house(float alpha, float s, float& beta, float& tau, float& sc) {
+  if (s == 0.f) {
+    beta = alpha; tau = 0.f; sc = 0.f;
+    return;
+  }
+  const float nrm = sqrtf(fmaf(alpha, alpha, s));
+  beta = (alpha >= 0.f) ? -nrm : nrm;
+  sc = __fdividef(1.f, alpha - beta);
+  tau = __fdividef(2.f, fmaf(s, sc * sc, 1.f));
+}
+
+// sum over the sixteen lanes of a half warp (butterfly: every lane gets the
+// same bits)
+__device__ __forceinline__ float half_sum(float v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 8);
+  return v;
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_svd_left(const float* __restrict__ Kg,
+                                                           long long sK, int m, int n,
+                                                           float* __restrict__ Ug, long long sU,
+                                                           float* __restrict__ Utg, long long sUt,
+                                                           double* __restrict__ lamg,
+                                                           long long slam, int r, int nlam,
+                                                           int* __restrict__ status) {
   extern __shared__ __align__(16) float sm[];
-  const SvdLayout Ly = svd_layout(m, n, r);
   const int p = m < n ? m : n;
-  const int N = Ly.N, ldk = Ly.ldk, zld = Ly.zld;
-  float* Kr = sm;                    // m x ldk, then r x zld (Golub-Kahan vectors)
-  float* Refl = sm + Ly.region;      // packed left reflectors
-  float* dd = Refl + Ly.refl;        // 128: diagonal of B
-  float* ee = dd + kNmax;            // 128: superdiagonal of B
-  float* tau = ee + kNmax;           // 128: left reflector scalars
-  float* Uw = tau + kNmax;           // 128: current left reflector (zero outside k..m-1)
-  float* W = Uw + kNmax;             // 128: tau K^T u, then row k of the updated K
-  float* V = W + kNmax;              // 128: current right reflector (zero outside)
-  float* Z = V + kNmax;              // 128: tau' (K - u w^T) v
-  float* lam = Z + kNmax;            // 128: sigma, descending
-  float* e2 = lam + kNmax;           // 256: squared Golub-Kahan off-diagonals
-  float* gk = e2 + 2 * kNmax;        // 256: the off-diagonals themselves
+  const int N = (m < n) ? 2 * p + 1 : 2 * p;
+  const int mr = (m + 3) & ~3;
+  float* Refl = sm;                                   // packed left reflectors
+  float* Zs = Refl + ((refl_total(m, p) + 3) & ~3);   // r x kRld: u parts of T_GK vectors
+  float* Xc = Zs + r * kRld;                          // 2 x 128: published column
+  float* Xr = Xc + 256;                               // 2 x 128: published row
+  float* Wp = Xr + 256;                               // 8 x 128: per-warp u^T K partials
+  float* dd = Wp + 1024;                              // diagonal of B
+  float* ee = dd + kNmax;                             // superdiagonal of B
+  float* tau = ee + kNmax;                            // left reflector scalars
+  float* lam = tau + kNmax;                           // sigma, descending
+  float* e2 = lam + kNmax;                            // 256: squared T_GK off-diagonals
+  float* gk = e2 + 2 * kNmax;                         // 256: the off-diagonals
   int* gcnt = reinterpret_cast<int*>(gk + 2 * kNmax);  // 256
-  float* pub = reinterpret_cast<float*>(gcnt + 2 * kNmax);  // 2 x 132
-  float* shift = pub + 2 * 132;      // 64
-  float* scal = shift + 64;          // 16
+  float* pub = reinterpret_cast<float*>(gcnt + 2 * kNmax);  // 2 x kRld
+  float* shift = pub + 2 * kRld;                      // 64
+  float* scal = shift + 64;                           // 16
+  int* roff = reinterpret_cast<int*>(scal + 16);      // 132: reflector offsets
+  float* Zb = reinterpret_cast<float*>(roff + 132);   // 128: per-warp row sums
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int b = blockIdx.x;
+  const int ta = 2 * warp + (lane >> 4), tb = lane & 15;
+  const int r0 = 8 * ta, c0 = 8 * tb;
   const float* K = Kg + (long long)b * sK;
 
-  // ---- load K, screen for NaN/Inf
+  // ---- load the tile, screen for NaN/Inf
+  float kt[8][8];
   bool bad = false;
-  for (int i = warp; i < m; i += kThreads / 32)
-    for (int j = lane; j < n; j += 32) {
-      const float x = K[(long long)i * n + j];
+#pragma unroll
+  for (int ii = 0; ii < 8; ++ii)
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+      const int row = r0 + ii, col = c0 + jj;
+      const float x = (row < m && col < n) ? K[(long long)row * n + col] : 0.f;
       if (!isfinite(x)) bad = true;
-      Kr[i * ldk + j] = x;
+      kt[ii][jj] = x;
     }
+  if (tid == 0) {
+    int t = 0;
+    for (int k = 0; k < p; ++k) {
+      roff[k] = t;
+      t += refl_len(k, m);
+    }
+  }
   if (__syncthreads_or(bad)) {
     for (int idx = tid; idx < m * r; idx += kThreads) Ug[(long long)b * sU + idx] = 0.f;
     if (Utg)
@@ -208,128 +280,241 @@ __global__ void __launch_bounds__(kThreads) k_svd_left(const float* __restrict__
     if (tid == 0) status[b] = TN_ERR_NONFINITE;
     return;
   }
+  // publish column 0 and row 0
+  if (tb == 0)
+#pragma unroll
+    for (int ii = 0; ii < 8; ++ii) Xc[r0 + ii] = kt[ii][0];
+  if (ta == 0)
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) Xr[c0 + jj] = kt[0][jj];
+  __syncthreads();
 
-  // ---- a. Golub-Kahan bidiagonalisation
+  // ---- a. Golub-Kahan bidiagonalisation.  A warp whose rows all lie above
+  // row k has nothing left to do but meet the barriers; warp 7 (rows 112 ..
+  // 127) is never idle and records d_k, e_k and tau_k.
   for (int k = 0; k < p; ++k) {
-    // A: left reflector from column k, rows k .. m-1 (warp 0)
-    if (warp == 0) {
-      float s = 0.f;
-      for (int i = k + 1 + lane; i < m; i += 32) {
-        const float x = Kr[i * ldk + k];
-        s = fmaf(x, x, s);
-      }
-      s = warp_sum(s);
-      const float alpha = Kr[k * ldk + k];
-      float tk, beta, sc;
-      if (s == 0.f) {
-        tk = 0.f; beta = alpha; sc = 0.f;
-      } else {
-        beta = -copysignf(sqrtf(alpha * alpha + s), alpha);
-        tk = (beta - alpha) / beta;
-        sc = 1.f / (alpha - beta);
-      }
-      const int ro = refl_off(k, m);
-      for (int i = lane; i < kNmax; i += 32) {
-        float u = 0.f;
-        if (i == k) u = 1.f;
-        else if (i > k && i < m && tk != 0.f) u = Kr[i * ldk + k] * sc;
-        Uw[i] = u;
-        if (i > k && i < m) Refl[ro + (i - k - 1)] = u;
-      }
-      if (lane == 0) {
-        dd[k] = beta;
-        tau[k] = tk;
-      }
-    }
-    __syncthreads();
-    // B: w_j = tau sum_i u_i K[i][j] (j > k), two threads per column with the
-    // rows split in halves; W[j] = row k of the updated K, K[k][j] - w_j
-    {
-      const float tk = tau[k];
-      const int j = tid >> 1, h = tid & 1;
-      const int mid = (k + m + 1) >> 1;
-      const int i0 = h ? mid : k, i1 = h ? m : mid;
-      float s = 0.f;
-      if (j > k && j < n && tk != 0.f)
-        for (int i = i0; i < i1; ++i) s = fmaf(Uw[i], Kr[i * ldk + j], s);
-      s += __shfl_xor_sync(0xffffffffu, s, 1);
-      if (h == 0 && j < kNmax) {
-        const float w = tk * s;
-        Z[j] = (j > k && j < n) ? w : 0.f;  // w, kept for the update
-        W[j] = (j > k && j < n) ? Kr[k * ldk + j] - w : 0.f;
-      }
-    }
-    __syncthreads();
-    // C: right reflector from row k, columns k+1 .. n-1 (warp 0); also w . v
-    if (warp == 0) {
-      float tq = 0.f, beta = 0.f, sc = 0.f;
-      if (k + 1 < n) {
-        float s = 0.f;
-        for (int j = k + 2 + lane; j < n; j += 32) s = fmaf(W[j], W[j], s);
-        s = warp_sum(s);
-        const float alpha = W[k + 1];
-        if (s == 0.f) {
-          tq = 0.f; beta = alpha;
-        } else {
-          beta = -copysignf(sqrtf(alpha * alpha + s), alpha);
-          tq = (beta - alpha) / beta;
-          sc = 1.f / (alpha - beta);
+    const float* xc = Xc + (k & 1) * 128;
+    const float* xr = Xr + (k & 1) * 128;
+    const bool wact = 16 * warp + 15 >= k;  // warp-uniform
+    float u[8], tk = 0.f;
+    if (wact) {
+      // left reflector from column k (every warp, same values)
+      float sc;
+      {
+        const float4 x4 = *reinterpret_cast<const float4*>(xc + 4 * lane);
+        const int i0 = 4 * lane;
+        float t = (i0 > k && i0 < m) ? x4.x * x4.x : 0.f;
+        t = (i0 + 1 > k && i0 + 1 < m) ? fmaf(x4.y, x4.y, t) : t;
+        t = (i0 + 2 > k && i0 + 2 < m) ? fmaf(x4.z, x4.z, t) : t;
+        t = (i0 + 3 > k && i0 + 3 < m) ? fmaf(x4.w, x4.w, t) : t;
+        const float s = warp_sum(t);
+        float beta;
+        house(xc[k], s, beta, tk, sc);
+        if (warp == 7 && lane == 0) {
+          dd[k] = beta;
+          tau[k] = tk;
         }
       }
+      {
+        const float4 xa = *reinterpret_cast<const float4*>(xc + r0);
+        const float4 xb = *reinterpret_cast<const float4*>(xc + r0 + 4);
+        const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+#pragma unroll
+        for (int ii = 0; ii < 8; ++ii) {
+          const int row = r0 + ii;
+          u[ii] = (row == k) ? 1.f : ((row > k && row < m) ? xv[ii] * sc : 0.f);
+        }
+      }
+      if (tb == 0) {  // keep reflector k for the back-transformation
+        const int P0 = k & ~3;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int row = r0 + 4 * h;
+          if (row >= P0 && row < mr)
+            *reinterpret_cast<float4*>(Refl + roff[k] + rpad(row) - rpad(P0)) =
+                make_float4(u[4 * h], u[4 * h + 1], u[4 * h + 2], u[4 * h + 3]);
+        }
+      }
+      // column sums u^T K over this warp's two tile rows (packed FMAs)
+      float2 cp[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) cp[q] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int ii = 0; ii < 8; ++ii) {
+        const float2 uu = make_float2(u[ii], u[ii]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          cp[q] = __ffma2_rn(uu, make_float2(kt[ii][2 * q], kt[ii][2 * q + 1]), cp[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        cp[q].x += __shfl_xor_sync(0xffffffffu, cp[q].x, 16);
+        cp[q].y += __shfl_xor_sync(0xffffffffu, cp[q].y, 16);
+      }
+      if (lane < 16) {  // [warp][half][tile column][4]: conflict-free float4 rows
+        *reinterpret_cast<float4*>(Wp + warp * 128 + 4 * tb) =
+            make_float4(cp[0].x, cp[0].y, cp[1].x, cp[1].y);
+        *reinterpret_cast<float4*>(Wp + warp * 128 + 64 + 4 * tb) =
+            make_float4(cp[2].x, cp[2].y, cp[3].x, cp[3].y);
+      }
+    }
+    __syncthreads();
+    if (wact) {
+      // w = tau K^T u and the updated row k, y = K[k][.] - w, for this
+      // thread's columns (the same sums in every thread of a tile column)
+      float w[8], y[8];
+      {
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) w[jj] = 0.f;
+        const int wmin = k >> 4;
+#pragma unroll
+        for (int ww = 0; ww < 8; ++ww) {
+          if (ww < wmin) continue;
+          const float4 pa = *reinterpret_cast<const float4*>(Wp + ww * 128 + 4 * tb);
+          const float4 pb = *reinterpret_cast<const float4*>(Wp + ww * 128 + 64 + 4 * tb);
+          w[0] += pa.x; w[1] += pa.y; w[2] += pa.z; w[3] += pa.w;
+          w[4] += pb.x; w[5] += pb.y; w[6] += pb.z; w[7] += pb.w;
+        }
+        const float4 ra = *reinterpret_cast<const float4*>(xr + c0);
+        const float4 rb = *reinterpret_cast<const float4*>(xr + c0 + 4);
+        const float rv[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          const int col = c0 + jj;
+          const bool on = col > k && col < n;
+          w[jj] = on ? tk * w[jj] : 0.f;
+          y[jj] = on ? rv[jj] - w[jj] : 0.f;
+        }
+      }
+      // right reflector from y over columns k+1 .. n-1 (every half warp,
+      // same values)
+      float tq = 0.f, sc2 = 0.f;
+      {
+        float t = 0.f;
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj)
+          if (c0 + jj > k + 1) t = fmaf(y[jj], y[jj], t);
+        const float s2 = half_sum(t);
+        float yk1 = 0.f;
+        switch ((k + 1) & 7) {  // uniform: a static register index per case
+          case 0: yk1 = y[0]; break;
+          case 1: yk1 = y[1]; break;
+          case 2: yk1 = y[2]; break;
+          case 3: yk1 = y[3]; break;
+          case 4: yk1 = y[4]; break;
+          case 5: yk1 = y[5]; break;
+          case 6: yk1 = y[6]; break;
+          default: yk1 = y[7]; break;
+        }
+        const float alpha2 = __shfl_sync(0xffffffffu, yk1, (((k + 1) >> 3) & 15) + (lane & 16));
+        float beta2 = 0.f;
+        if (k + 1 < n) house(alpha2, s2, beta2, tq, sc2);
+        if (warp == 7 && lane == 0) ee[k] = beta2;
+      }
+      float v[8];
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        const int col = c0 + jj;
+        v[jj] = (col == k + 1 && k + 1 < n) ? 1.f : ((col > k + 1 && col < n) ? y[jj] * sc2 : 0.f);
+      }
       float wv = 0.f;
-      for (int j = lane; j < kNmax; j += 32) {
-        float v = 0.f;
-        if (j == k + 1 && k + 1 < n) v = 1.f;
-        else if (j > k + 1 && j < n && tq != 0.f) v = W[j] * sc;
-        V[j] = v;
-        wv = fmaf(Z[j], v, wv);
-      }
-      wv = warp_sum(wv);
-      if (lane == 0) {
-        ee[k] = beta;
-        scal[0] = tq;
-        scal[1] = wv;
-      }
-    }
-    __syncthreads();
-    // D: z_i = tau' (sum_j K[i][j] v_j - u_i (w . v)) for rows i > k, from
-    // the matrix before this step's update; two threads per row
-    const float tq = scal[0];
-    float zi = 0.f;
-    const int iz = k + 1 + (tid >> 1);
-    if (tq != 0.f) {
-      const int h = tid & 1;
-      const int midc = (k + 1 + n + 1) >> 1;
-      const int j0 = h ? midc : k + 1, j1 = h ? n : midc;
-      float s = 0.f;
-      if (iz < m)
-        for (int j = j0; j < j1; ++j) s = fmaf(Kr[iz * ldk + j], V[j], s);
-      s += __shfl_xor_sync(0xffffffffu, s, 1);
-      zi = tq * (s - Uw[iz < kNmax ? iz : 0] * scal[1]);
-    }
-    __syncthreads();  // every read of K for z done; W, Z (w) stable
-    // E: K[i][j] -= u_i w_j + z_i v_j for i, j > k; z_i travels through
-    // shared memory (the w copy in Z is read first into registers)
-    float wj[4], vj[4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int j = lane + 32 * c;
-      wj[c] = Z[j];
-      vj[c] = V[j];
-    }
-    __syncthreads();
-    if ((tid & 1) == 0 && iz < m) Z[iz] = zi;
-    __syncthreads();
-    for (int i = k + 1 + warp; i < m; i += kThreads / 32) {
-      const float ui = Uw[i], zr = (tq != 0.f) ? Z[i] : 0.f;
+      for (int jj = 0; jj < 8; ++jj) wv = fmaf(w[jj], v[jj], wv);
+      wv = half_sum(wv);
+      // row sums K v over a tile row: packed FMAs, then a reduce-scatter over
+      // the sixteen lanes (lane pair (b, b ^ 1) ends with row 4 b3 + 2 b2 + b1
+      // of the tile) and a gather through shared memory
+      float z[8];
+      {
+        float t[8];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int j = lane + 32 * c;
-        if (j > k && j < n) {
-          float x = Kr[i * ldk + j];
-          x = fmaf(-ui, wj[c], x);
-          x = fmaf(-zr, vj[c], x);
-          Kr[i * ldk + j] = x;
+        for (int ii = 0; ii < 8; ++ii) {
+          float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            acc = __ffma2_rn(make_float2(kt[ii][2 * q], kt[ii][2 * q + 1]),
+                             make_float2(v[2 * q], v[2 * q + 1]), acc);
+          t[ii] = acc.x + acc.y;
+        }
+        const bool h3 = tb & 8, h2 = tb & 4, h1 = tb & 2;
+        float a4[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float send = h3 ? t[i] : t[i + 4];
+          const float keep = h3 ? t[i + 4] : t[i];
+          a4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        }
+        float a2[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          const float send = h2 ? a4[i] : a4[i + 2];
+          const float keep = h2 ? a4[i + 2] : a4[i];
+          a2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+        }
+        float a1;
+        {
+          const float send = h1 ? a2[0] : a2[1];
+          const float keep = h1 ? a2[1] : a2[0];
+          a1 = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+        }
+        a1 += __shfl_xor_sync(0xffffffffu, a1, 1);
+        float* zb = Zb + warp * 16 + (lane >> 4) * 8;
+        if ((tb & 1) == 0) zb[(h3 ? 4 : 0) + (h2 ? 2 : 0) + (h1 ? 1 : 0)] = a1;
+        __syncwarp();
+        const float4 za = *reinterpret_cast<const float4*>(zb);
+        const float4 zc = *reinterpret_cast<const float4*>(zb + 4);
+        const float zr[8] = {za.x, za.y, za.z, za.w, zc.x, zc.y, zc.z, zc.w};
+#pragma unroll
+        for (int ii = 0; ii < 8; ++ii) {
+          const int row = r0 + ii;
+          z[ii] = (row > k) ? tq * fmaf(-u[ii], wv, zr[ii]) : 0.f;
+        }
+      }
+      // K -= u w^T + z v^T (packed FMAs)
+      if (r0 + 7 > k && c0 + 7 > k) {
+#pragma unroll
+        for (int ii = 0; ii < 8; ++ii) {
+          const float2 nu = make_float2(-u[ii], -u[ii]), nz = make_float2(-z[ii], -z[ii]);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            float2 x = __ffma2_rn(nu, make_float2(w[2 * q], w[2 * q + 1]),
+                                  make_float2(kt[ii][2 * q], kt[ii][2 * q + 1]));
+            x = __ffma2_rn(nz, make_float2(v[2 * q], v[2 * q + 1]), x);
+            kt[ii][2 * q] = x.x;
+            kt[ii][2 * q + 1] = x.y;
+          }
+        }
+      }
+    }
+    // publish column k+1 and row k+1 for the next step (rows above k + 1,
+    // held by idle warps, are masked by every reader)
+    if (k + 1 < p && wact) {
+      const int cn = k + 1;
+      float* xcn = Xc + (cn & 1) * 128;
+      float* xrn = Xr + (cn & 1) * 128;
+      if (tb == (cn >> 3)) {
+        switch (cn & 7) {
+#define TN_PUB_COL(E) \
+  case E: {           \
+    _Pragma("unroll") for (int ii = 0; ii < 8; ++ii) xcn[r0 + ii] = kt[ii][E]; \
+  } break;
+          TN_PUB_COL(0) TN_PUB_COL(1) TN_PUB_COL(2) TN_PUB_COL(3)
+          TN_PUB_COL(4) TN_PUB_COL(5) TN_PUB_COL(6) TN_PUB_COL(7)
+#undef TN_PUB_COL
+        }
+      }
+      if (ta == (cn >> 3)) {
+        switch (cn & 7) {
+#define TN_PUB_ROW(E)                                                            \
+  case E: {                                                                      \
+    *reinterpret_cast<float4*>(xrn + c0) =                                       \
+        make_float4(kt[E][0], kt[E][1], kt[E][2], kt[E][3]);                     \
+    *reinterpret_cast<float4*>(xrn + c0 + 4) =                                   \
+        make_float4(kt[E][4], kt[E][5], kt[E][6], kt[E][7]);                     \
+  } break;
+          TN_PUB_ROW(0) TN_PUB_ROW(1) TN_PUB_ROW(2) TN_PUB_ROW(3)
+          TN_PUB_ROW(4) TN_PUB_ROW(5) TN_PUB_ROW(6) TN_PUB_ROW(7)
+#undef TN_PUB_ROW
         }
       }
     }
@@ -347,8 +532,8 @@ __global__ void __launch_bounds__(kThreads) k_svd_left(const float* __restrict__
   if (tid == 0) {
     float gu = 0.f, emax = 0.f;
     for (int j = 0; j < N; ++j) {
-      const float gl_ = (j > 0) ? sqrtf(e2[j - 1]) : 0.f;
-      const float gr_ = (j + 1 < N) ? sqrtf(e2[j]) : 0.f;
+      const float gl_ = (j > 0) ? fabsf(gk[j - 1]) : 0.f;
+      const float gr_ = (j + 1 < N) ? fabsf(gk[j]) : 0.f;
       gu = fmaxf(gu, gl_ + gr_);
       if (j + 1 < N) emax = fmaxf(emax, e2[j]);
     }
@@ -384,7 +569,7 @@ __global__ void __launch_bounds__(kThreads) k_svd_left(const float* __restrict__
       }
       float lo = (m0 > 0) ? fmaf(hg, float(m0), gl) : gl;
       float hi = (m0 < kThreads) ? fmaf(hg, float(m0 + 1), gl) : gu;
-      for (int it = 0; it < 10; ++it) {
+      for (int it = 0; it < 9; ++it) {
         const float h = (hi - lo) / 5.f;
         const float x = fmaf(h, float(q + 1), lo);
         const int cnt = valid ? sturm_gk(e2, N, x, pivmin) : 0;
@@ -410,13 +595,12 @@ __global__ void __launch_bounds__(kThreads) k_svd_left(const float* __restrict__
   __syncthreads();
 
   // ---- c. inverse iteration on T_GK - sigma I, one thread per vector, two
-  // solves from a fixed pseudo-random start; the solution lives in this
-  // thread's column of the region (K is no longer needed), the triangular
-  // factor (rows divided by their pivots) in local memory
-  float* Zs = Kr;
+  // solves from a fixed pseudo-random start; solution and triangular factor
+  // (rows divided by their pivots) in local memory; the odd entries (the
+  // left singular vector of B), max-abs normalised, go to the thread's padded
+  // row of Zs
   if (tid < r) {
-    float u2[2 * kNmax + 1], u3[2 * kNmax + 1];
-    float* y = Zs + tid * zld;
+    float y[2 * kNmax + 1], u2[2 * kNmax + 1], u3[2 * kNmax + 1];
     auto start = [&](int i) {
       unsigned int hsh = 2654435761u * (unsigned)(i + 1) ^ (40503u * (unsigned)(tid + 7));
       hsh ^= hsh >> 13; hsh *= 0x5bd1e995u; hsh ^= hsh >> 15;
@@ -429,25 +613,34 @@ __global__ void __launch_bounds__(kThreads) k_svd_left(const float* __restrict__
       float a = -lmb;
       float bb = (N > 1) ? gk[0] : 0.f;
       float yk = (it == 0) ? start(0) : y[0] * inv;
-      for (int i = 0; i + 1 < N; ++i) {
-        const float c = gk[i];
-        const float nd = -lmb;
-        const float ns = (i + 2 < N) ? gk[i + 1] : 0.f;
-        const float yn = (it == 0) ? start(i + 1) : y[i + 1] * inv;
-        const bool piv = fabsf(a) >= fabsf(c);
-        const float den = piv ? ((a == 0.f) ? tp : a) : c;
-        const float rd = 1.f / den;
-        const float mlt = (piv ? c : a) * rd;
-        const float yo = piv ? yk : yn, ye = piv ? yn : yk;
-        u2[i] = (piv ? bb : nd) * rd;
-        u3[i] = piv ? 0.f : ns * rd;
-        y[i] = yo * rd;
-        yk = fmaf(-mlt, yo, ye);
-        a = piv ? fmaf(-mlt, bb, nd) : fmaf(-mlt, nd, bb);
-        bb = piv ? ns : -mlt * ns;
+      for (int i0 = 0; i0 + 1 < N; i0 += 8) {
+        float yg[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int i = i0 + q;
+          yg[q] = (i + 1 < N) ? ((it == 0) ? start(i + 1) : y[i + 1] * inv) : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int i = i0 + q;
+          if (i + 1 >= N) break;
+          const float c = gk[i];
+          const float ns = (i + 2 < N) ? gk[i + 1] : 0.f;
+          const bool piv = fabsf(a) >= fabsf(c);
+          const float den = piv ? ((a == 0.f) ? tp : a) : c;
+          const float rd = __fdividef(1.f, den);
+          const float mlt = (piv ? c : a) * rd;
+          const float yo = piv ? yk : yg[q], ye = piv ? yg[q] : yk;
+          u2[i] = (piv ? bb : -lmb) * rd;
+          u3[i] = piv ? 0.f : ns * rd;
+          y[i] = yo * rd;
+          yk = fmaf(-mlt, yo, ye);
+          a = piv ? fmaf(-mlt, bb, -lmb) : fmaf(-mlt, -lmb, bb);
+          bb = piv ? ns : -mlt * ns;
+        }
       }
       if (a == 0.f) a = tp;
-      float x2 = yk / a;
+      float x2 = __fdividef(yk, a);
       y[N - 1] = x2;
       float x1 = x2;
       float mx = fabsf(x2);
@@ -456,32 +649,49 @@ __global__ void __launch_bounds__(kThreads) k_svd_left(const float* __restrict__
         y[N - 2] = x1;
         mx = fmaxf(mx, fabsf(x1));
       }
-      for (int i = N - 3; i >= 0; --i) {
-        const float xi = y[i] - u2[i] * x1 - u3[i] * x2;
-        y[i] = xi;
-        mx = fmaxf(mx, fabsf(xi));
-        x2 = x1;
-        x1 = xi;
+      for (int i0 = N - 3; i0 >= 0; i0 -= 8) {
+        float yg[8], ag[8], bg[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int i = i0 - q;
+          yg[q] = (i >= 0) ? y[i] : 0.f;
+          ag[q] = (i >= 0) ? u2[i] : 0.f;
+          bg[q] = (i >= 0) ? u3[i] : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int i = i0 - q;
+          if (i < 0) break;
+          const float xi = yg[q] - ag[q] * x1 - bg[q] * x2;
+          y[i] = xi;
+          mx = fmaxf(mx, fabsf(xi));
+          x2 = x1;
+          x1 = xi;
+        }
       }
       inv = (mx > 0.f && isfinite(mx)) ? 1.f / mx : 1.f;
     }
-    shift[tid] = inv;  // read back as the vector's scale
+    float* zo = Zs + tid * kRld;
+    for (int i = 0; i < p; ++i) zo[rpad(i)] = y[2 * i + 1] * inv;
+    for (int i = p; i < kNmax; ++i) zo[rpad(i)] = 0.f;
   }
   __syncthreads();
 
-  // ---- d. vectors: thread quad (column col, quarter qr) holds rows
-  // kk * 4 + qr of its vector: the odd entries of the T_GK vector
+  // ---- d. vectors: thread quad (column col, quarter qr), rows 32 qr + kk
   const int col = tid >> 2, qr = tid & 3;
   const bool live = col < r;
   float z[kQ];
-  {
-    const float vs = live ? shift[col] : 0.f;
+  auto load32 = [&](const float* src, float* dst) {
 #pragma unroll
-    for (int kk = 0; kk < kQ; ++kk) {
-      const int row = kk * 4 + qr;
-      z[kk] = (live && row < p) ? Zs[col * zld + 2 * row + 1] * vs : 0.f;
+    for (int mm = 0; mm < kQ / 4; ++mm) {
+      const float4 t = *reinterpret_cast<const float4*>(src + qr * 36 + 4 * mm);
+      dst[4 * mm] = t.x; dst[4 * mm + 1] = t.y; dst[4 * mm + 2] = t.z; dst[4 * mm + 3] = t.w;
     }
-  }
+  };
+  if (live) load32(Zs + col * kRld, z);
+  else
+#pragma unroll
+    for (int kk = 0; kk < kQ; ++kk) z[kk] = 0.f;
   auto dot32 = [](const float* x, const float* y2) {
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
@@ -493,42 +703,42 @@ __global__ void __launch_bounds__(kThreads) k_svd_left(const float* __restrict__
     }
     return (a0 + a1) + (a2 + a3);
   };
-  __syncthreads();  // Zs reads done before pub writes (pub is separate, but keep order simple)
   auto normalise_publish = [&](float* dst) {
     const float s = quad_sum(dot32(z, z));
     const float iv = (s > 0.f) ? 1.f / sqrtf(s) : 0.f;
 #pragma unroll
-    for (int kk = 0; kk < kQ; ++kk) {
-      z[kk] *= iv;
-      dst[kk * 4 + qr] = z[kk];
-    }
+    for (int kk = 0; kk < kQ; ++kk) z[kk] *= iv;
+#pragma unroll
+    for (int mm = 0; mm < kQ / 4; ++mm)
+      *reinterpret_cast<float4*>(dst + qr * 36 + 4 * mm) =
+          make_float4(z[4 * mm], z[4 * mm + 1], z[4 * mm + 2], z[4 * mm + 3]);
   };
   if (col == 0) normalise_publish(pub);
   for (int j = 0; j < r; ++j) {
     __syncthreads();  // vector j published; reads of the other buffer done
     if (live && col > j) {
-      const float* pv = pub + (j & 1) * 132;
       float pj[kQ];
-#pragma unroll
-      for (int kk = 0; kk < kQ; ++kk) pj[kk] = pv[kk * 4 + qr];
+      load32(pub + (j & 1) * kRld, pj);
       const float d = quad_sum(dot32(pj, z));
 #pragma unroll
       for (int kk = 0; kk < kQ; ++kk) z[kk] = fmaf(-d, pj[kk], z[kk]);
-      if (col == j + 1) normalise_publish(pub + ((j + 1) & 1) * 132);
+      if (col == j + 1) normalise_publish(pub + ((j + 1) & 1) * kRld);
     }
   }
   if (live) {
-    // U = H_0 ... H_{p-1} [u; 0]: reflector k covers rows k .. m-1 with
-    // entry 1 at row k and the packed entries below
+    // U = H_0 ... H_{p-1} [u; 0]
     for (int k = p - 1; k >= 0; --k) {
       const float tk = tau[k];
       if (tk == 0.f) continue;
-      const int ro = refl_off(k, m);
+      const int P0 = k & ~3;
+      const float* rk = Refl + roff[k] - rpad(P0);
       float vk[kQ];
 #pragma unroll
-      for (int kk = 0; kk < kQ; ++kk) {
-        const int row = kk * 4 + qr;
-        vk[kk] = (row == k) ? 1.f : ((row > k && row < m) ? Refl[ro + row - k - 1] : 0.f);
+      for (int mm = 0; mm < kQ / 4; ++mm) {
+        const int row = 32 * qr + 4 * mm;
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (row >= P0 && row < mr) t = *reinterpret_cast<const float4*>(rk + qr * 36 + 4 * mm);
+        vk[4 * mm] = t.x; vk[4 * mm + 1] = t.y; vk[4 * mm + 2] = t.z; vk[4 * mm + 3] = t.w;
       }
       const float d = quad_sum(dot32(vk, z)) * tk;
 #pragma unroll
@@ -538,9 +748,9 @@ __global__ void __launch_bounds__(kThreads) k_svd_left(const float* __restrict__
     int bi = kNmax;
 #pragma unroll
     for (int kk = 0; kk < kQ; ++kk) {
-      const int row = kk * 4 + qr;
-      const float a = fabsf(z[kk]);
-      if (row < m && (a > best || (a == best && row < bi))) { best = a; bi = row; }
+      const int row = 32 * qr + kk;
+      const float av = fabsf(z[kk]);
+      if (row < m && (av > best || (av == best && row < bi))) { best = av; bi = row; }
     }
     const unsigned qm = 0xFu << (threadIdx.x & 28);
     for (int o = 1; o <= 2; o <<= 1) {
@@ -551,14 +761,14 @@ __global__ void __launch_bounds__(kThreads) k_svd_left(const float* __restrict__
     float sv = 0.f;
 #pragma unroll
     for (int kk = 0; kk < kQ; ++kk)
-      if (kk * 4 + qr == bi) sv = z[kk];
+      if (32 * qr + kk == bi) sv = z[kk];
     sv = quad_sum(sv);
     const float sg = (sv < 0.f) ? -1.f : 1.f;
     float* U = Ug + (long long)b * sU;
     float* Ut = Utg ? Utg + (long long)b * sUt + (long long)col * m : nullptr;
 #pragma unroll
     for (int kk = 0; kk < kQ; ++kk) {
-      const int row = kk * 4 + qr;
+      const int row = 32 * qr + kk;
       if (row < m) {
         U[(long long)row * r + col] = sg * z[kk];
         if (Ut) Ut[row] = sg * z[kk];
@@ -568,8 +778,8 @@ __global__ void __launch_bounds__(kThreads) k_svd_left(const float* __restrict__
   if (lamg) {
     double* lo = lamg + (long long)b * slam;
     for (int t = tid; t < nlam; t += kThreads) {
-      const double s = (t < nl) ? double(lam[t]) : 0.0;
-      lo[t] = s * s;
+      const double sv = (t < nl) ? double(lam[t]) : 0.0;
+      lo[t] = sv * sv;
     }
   }
 }
@@ -588,8 +798,9 @@ cudaError_t launch_chol_env(float* R, long long sR, const int64_t* r_off, const 
 }
 
 size_t svd_left_smem_bytes(int m, int n, int r) {
-  const SvdLayout L = svd_layout(m, n, r);
-  return sizeof(float) * (size_t(L.region) + size_t(L.refl) + size_t(kSmallFloats));
+  const int p = m < n ? m : n;
+  return sizeof(float) *
+         (size_t((refl_total(m, p) + 3) & ~3) + size_t(r) * kRld + size_t(kSmallFloats));
 }
 
 bool svd_left_supported(int m, int n, int r) {
