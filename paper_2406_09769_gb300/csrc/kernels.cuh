@@ -146,7 +146,6 @@ cudaError_t launch_svd_left(const float* K, long long sK, int m, int n, float* U
                             int nlam, int* status, int batch, cudaStream_t st);
 bool svd_left_supported(int m, int n, int r);
 size_t svd_left_smem_bytes(int m, int n, int r);
-size_t chol_env_smem_bytes(int n);
 cudaError_t svd_configure();
 
 template <typename T>

@@ -59,66 +59,96 @@ __device__ __forceinline__ float quad_sum(float v) {
 }
 
 // ------------------------------------------------------------- Cholesky
-// One CTA per (instance, tree vertex k): R = R_k / max|R_k| (symmetrised),
-// right-looking unblocked Cholesky R = C C^T in FP32.  Step j reads column j
-// and the pivot, both final since step j - 1, and updates the trailing lower
-// triangle; column j is scaled only at the store.  A pivot that is not
-// positive (round-off of a semi-definite R) leaves column j zero and the
+// One CTA per (instance, tree vertex k): A = (R_k + R_k^T) / (2 max|R_k|),
+// right-looking unblocked Cholesky A = C C^T in FP32 with the matrix in
+// registers, thread (a = 2 warp + lane / 16, b = lane % 16) holding the 8 x 8
+// tile A[8a .. 8a+7][8b .. 8b+7].  Step j: the owners of column j published
+// it; every thread takes the pivot and its rows' and columns' entries of
+// column j (A is kept symmetric, so row j equals column j), updates its tile
+// A -= a_j a_j^T / pivot on rows and columns beyond j, and the owners of
+// column j + 1 publish it: one barrier per step.  Row j of the output, C^T,
+// is written straight from the published column.  A pivot that is not
+// positive (round-off of a semi-definite R) leaves column j of C zero and the
 // trailing block untouched.  Output in place of R_k: B[j][l] = C[l][j]
 // (row-major, upper triangular), the K-major second operand of K = M C.
-__global__ void __launch_bounds__(kThreads) k_chol_env(float* __restrict__ R, long long sR,
-                                                        const int64_t* __restrict__ r_off,
-                                                        const int32_t* __restrict__ D,
-                                                        const unsigned int* __restrict__ amax,
-                                                        long long s_amax, int k0, int nk) {
-  extern __shared__ __align__(16) float ch[];
+__global__ void __launch_bounds__(kThreads, 2) k_chol_env(float* __restrict__ R, long long sR,
+                                                          const int64_t* __restrict__ r_off,
+                                                          const int32_t* __restrict__ D,
+                                                          const unsigned int* __restrict__ amax,
+                                                          long long s_amax, int k0, int nk) {
+  __shared__ __align__(16) float Xc[2][128];
   const int b = blockIdx.x / nk;
   const int k = k0 + blockIdx.x % nk;
   const int n = D[k];
-  const int ld = n | 1;  // odd pitch: column reads hit distinct banks
-  float* A = ch;
-  float* rs = ch + n * ld;  // 1 / sqrt(pivot), or 0
   float* Rg = R + (long long)b * sR + r_off[k];
   const float am = __uint_as_float(amax[(long long)b * s_amax + k]);
-  const float sc = (am > 0.f && isfinite(am)) ? 1.f / am : 1.f;
-  const int tid = threadIdx.x;
-  for (int idx = tid; idx < n * n; idx += kThreads) {
-    const int i = idx / n, j = idx - i * n;
-    A[i * ld + j] = Rg[idx] * sc;
-  }
-  __syncthreads();
-  for (int idx = tid; idx < n * n; idx += kThreads) {
-    const int i = idx / n, j = idx - i * n;
-    if (j < i) {
-      const float x = 0.5f * (A[i * ld + j] + A[j * ld + i]);
-      A[i * ld + j] = x;  // lower triangle only from here on
+  const float sc = (am > 0.f && isfinite(am)) ? 0.5f / am : 0.5f;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ta = 2 * warp + (lane >> 4), tb = lane & 15;
+  const int r0 = 8 * ta, c0 = 8 * tb;
+  float t[8][8];
+#pragma unroll
+  for (int ii = 0; ii < 8; ++ii)
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+      const int i = r0 + ii, c = c0 + jj;
+      t[ii][jj] = (i < n && c < n) ? (Rg[(long long)i * n + c] + Rg[(long long)c * n + i]) * sc
+                                   : 0.f;
     }
-  }
-  __syncthreads();
-  // thread pair per row: row i = k + 1 + (tid >> 1) (+128 for the second
-  // pass), the two lanes take alternate columns
+  if (tb == 0)
+#pragma unroll
+    for (int ii = 0; ii < 8; ++ii) Xc[0][r0 + ii] = t[ii][0];
+  __syncthreads();  // every load of R_k done before the first store of C^T
   for (int j = 0; j < n; ++j) {
-    const float p = A[j * ld + j];
-    if (p > 0.f && isfinite(p)) {
-      const float ip = 1.f / p;
-      for (int i = j + 1 + (tid >> 1); i < n; i += kThreads / 2) {
-        const float aij = A[i * ld + j] * ip;
-        for (int c = j + 1 + (tid & 1); c <= i; c += 2) A[i * ld + c] -= aij * A[c * ld + j];
+    const float* xc = Xc[j & 1];
+    const float p = xc[j];
+    const bool ok = p > 0.f && isfinite(p);
+    const float ip = ok ? 1.f / p : 0.f;
+    const float rs = ok ? rsqrtf(p) : 0.f;
+    // row j of C^T: C[l][j] = a_lj / sqrt(p) below the diagonal, sqrt(p) on it
+    for (int l = tid; l < n; l += kThreads) {
+      float v = 0.f;
+      if (ok && l > j) v = xc[l] * rs;
+      else if (ok && l == j) v = p * rs;
+      Rg[(long long)j * n + l] = v;
+    }
+    if (ok && r0 + 7 > j && c0 + 7 > j) {
+      const float4 ra = *reinterpret_cast<const float4*>(xc + r0);
+      const float4 rb = *reinterpret_cast<const float4*>(xc + r0 + 4);
+      const float4 ca = *reinterpret_cast<const float4*>(xc + c0);
+      const float4 cb = *reinterpret_cast<const float4*>(xc + c0 + 4);
+      const float rv[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
+      const float cv[8] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+      float cm[8];
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) cm[jj] = (c0 + jj > j) ? cv[jj] * ip : 0.f;
+#pragma unroll
+      for (int ii = 0; ii < 8; ++ii) {
+        const float ri = (r0 + ii > j) ? rv[ii] : 0.f;
+        const float2 nr = make_float2(-ri, -ri);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float2 x = __ffma2_rn(nr, make_float2(cm[2 * q], cm[2 * q + 1]),
+                                      make_float2(t[ii][2 * q], t[ii][2 * q + 1]));
+          t[ii][2 * q] = x.x;
+          t[ii][2 * q + 1] = x.y;
+        }
+      }
+    }
+    const int cn = j + 1;
+    if (cn < n && tb == (cn >> 3)) {
+      float* xn = Xc[cn & 1];
+      switch (cn & 7) {
+#define TN_CHOL_PUB(E) \
+  case E: {            \
+    _Pragma("unroll") for (int ii = 0; ii < 8; ++ii) xn[r0 + ii] = t[ii][E]; \
+  } break;
+        TN_CHOL_PUB(0) TN_CHOL_PUB(1) TN_CHOL_PUB(2) TN_CHOL_PUB(3)
+        TN_CHOL_PUB(4) TN_CHOL_PUB(5) TN_CHOL_PUB(6) TN_CHOL_PUB(7)
+#undef TN_CHOL_PUB
       }
     }
     __syncthreads();
-  }
-  for (int j = tid; j < n; j += kThreads) {
-    const float p = A[j * ld + j];
-    rs[j] = (p > 0.f && isfinite(p)) ? 1.f / sqrtf(p) : 0.f;
-  }
-  __syncthreads();
-  for (int idx = tid; idx < n * n; idx += kThreads) {
-    const int j = idx / n, l = idx - j * n;  // B[j][l] = C[l][j]
-    float v = 0.f;
-    if (l > j) v = A[l * ld + j] * rs[j];
-    else if (l == j) v = (rs[j] > 0.f) ? A[j * ld + j] * rs[j] : 0.f;
-    Rg[idx] = v;
   }
 }
 
@@ -786,14 +816,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_svd_left(const float* __restric
 
 }  // namespace
 
-size_t chol_env_smem_bytes(int n) { return sizeof(float) * (size_t(n) * (n | 1) + n); }
-
 cudaError_t launch_chol_env(float* R, long long sR, const int64_t* r_off, const int32_t* D,
                             int maxD, const unsigned int* amax, long long s_amax, int k0, int nk,
                             int batch, cudaStream_t st) {
   if (maxD < 1 || maxD > kNmax || nk < 1) return cudaErrorInvalidValue;
-  const size_t smem = chol_env_smem_bytes(maxD);
-  k_chol_env<<<batch * nk, kThreads, smem, st>>>(R, sR, r_off, D, amax, s_amax, k0, nk);
+  k_chol_env<<<batch * nk, kThreads, 0, st>>>(R, sR, r_off, D, amax, s_amax, k0, nk);
   return cudaGetLastError();
 }
 
@@ -825,12 +852,9 @@ cudaError_t svd_configure() {
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
   const size_t need_svd = svd_left_smem_bytes(kNmax, kNmax, kRmax);
-  const size_t need_chol = chol_env_smem_bytes(kNmax);
-  if (need_svd > size_t(optin) || need_chol > size_t(optin)) return cudaErrorInvalidValue;
-  e = cudaFuncSetAttribute(k_svd_left, cudaFuncAttributeMaxDynamicSharedMemorySize, int(need_svd));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_chol_env, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(need_chol));
+  if (need_svd > size_t(optin)) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(k_svd_left, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(need_svd));
 }
 
 }  // namespace tn
