@@ -31,14 +31,11 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-# Peaks used for roofline fractions.  Tensor peaks come from the measured
-# copy / cuBLAS numbers when available; ALU peaks are derived from unit counts
-# and clocks: FP32 = 152 SMs x 128 lanes x 2 flop x 2.07 GHz; FP64 = the
-# part's nominal 1.25 TFLOP/s.
+# Peaks for the roofline fractions.  The FP32, FP64 and TF32 tensor-pipe peaks
+# are measured in this run by the library's own burst kernels
+# (tn_measure_peaks); copy bandwidth and BF16 come from MEASURED_PEAKS.json
+# (else the fallback below).
 FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
-FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-FP64_ALU_TFLOPS = 1.25
-TF32_PER_BF16 = 1.1 / 2.25
 
 WORKLOAD = "2D Ising spin glass 32x32 open, J~N(0,1), beta=0.5, rows as partitions, MPS ansatz"
 
@@ -56,6 +53,8 @@ def parse():
     p.add_argument("--batch", type=int, default=304)
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-fp64-arm", action="store_true",
+                   help="skip the FP64-path measurement beside the headline (N=1 only)")
     return p.parse_args()
 
 
@@ -345,19 +344,22 @@ def bench_ours(args):
     flops = {"env": info["flops_env"], "local": info["flops_local"],
              "density": info["flops_density"], "project": info["flops_project"],
              "eig": info["flops_eig"]}
+    if prec == B.TN_PREC_TF32:  # factored density matrices (the planner's counts)
+        flops.update({"density": info["flops_kfactor"], "eig": info["flops_svd"],
+                      "factor": info["flops_factor"]})
     pk, pk_src = peaks()
+    mp = B.tn_measure_peaks(local)  # burst kernels, after the timed region
+    fp32_peak = max(mp["fp32"], mp["fp32x2"])
     dom = max(flops, key=lambda k: prof[k][1])
     n_l, ms = prof[dom]
     achieved = flops[dom] * Bn / (ms / 1e3) / 1e12
-    if prec == B.TN_PREC_FP64:
-        bound, peak, note = "alu", FP64_ALU_TFLOPS, "FP64 nominal 1.25 TFLOP/s (derived)"
-    elif dom == "eig":
-        bound, peak, note = "alu", FP32_ALU_TFLOPS, "FP32 152 SMs x 128 lanes x 2 x 2.07 GHz"
+    tensor = prec != B.TN_PREC_FP64 and dom in ("env", "local", "density", "project")
+    if tensor:
+        bound, peak, note = "tensor", mp["tf32"], "measured tcgen05 kind::tf32 burst (this run)"
+    elif prec == B.TN_PREC_FP64:
+        bound, peak, note = "alu", mp["fp64"], "measured FP64 FMA burst (this run)"
     else:
-        bf16 = pk.get("bf16_tflops_sustained", FALLBACK["bf16_tflops_sustained"])
-        is_tf32 = prec in (B.TN_PREC_TF32, B.TN_PREC_TF32_FAST, B.TN_PREC_TF32_GRAM)
-        peak = bf16 * (TF32_PER_BF16 if is_tf32 else 1.0)
-        bound, note = "tensor", f"{pk_src} bf16 sustained" + (" x 1.1/2.25 (tf32)" if is_tf32 else "")
+        bound, peak, note = "alu", fp32_peak, "measured FP32 FMA burst (this run)"
     # DRAM bytes per launch of the dominant kernel from an ncu capture; null when
     # the kernel's source has changed since the counters were taken
     traffic = None
@@ -380,15 +382,51 @@ def bench_ours(args):
     dm_ms = sum(prof[k][1] for k in dm_cls)
     dm_flops = sum(flops[k] for k in dm_cls) * Bn
     if prec == B.TN_PREC_FP64:
-        dm_peak, dm_note = FP64_ALU_TFLOPS, "FP64 ALU (no tensor cores)"
+        dm_peak, dm_note = mp["fp64"], "measured FP64 FMA burst (no tensor cores on this path)"
     else:
-        bf16 = pk.get("bf16_tflops_sustained", FALLBACK["bf16_tflops_sustained"])
-        dm_peak = bf16 * TF32_PER_BF16
-        dm_note = f"{pk_src} bf16 sustained x 1.1/2.25 (tf32)"
+        dm_peak, dm_note = mp["tf32"], "measured tcgen05 kind::tf32 burst (this run)"
     dm_group = {"achieved": dm_flops / (dm_ms / 1e3) / 1e12, "peak": dm_peak, "unit": "TFLOP/s",
                 "frac": dm_flops / (dm_ms / 1e3) / 1e12 / dm_peak, "ms_per_batch": dm_ms,
                 "peak_source": dm_note,
                 "note": "algorithmic flops; the compensated TF32 split issues 3 MMAs per product"}
+
+    # batch-1 latency: one instance from site tensors to ln Z
+    lat = None
+    if world == 1:
+        p1 = [plan]
+        for _ in range(3):
+            B.tn_contract_approx(ctx, p1, ptrs[:1], prec, 0, sh)
+            B.tn_logz(ctx, 1)
+        lt = []
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.tn_contract_approx(ctx, p1, ptrs[:1], prec, 0, sh)
+            e1.record(stream)
+            e1.synchronize()
+            lt.append(e0.elapsed_time(e1))
+        B.tn_logz(ctx, 1)
+        lat = {"batch": 1, "ms_per_contraction": statistics.median(lt),
+               "contractions_per_s": 1e3 / statistics.median(lt), "steps": 5, "warmup": 3}
+
+    # the FP64 path on the same batch (warm-up 1, one timed step), N = 1 only
+    fp64_arm = None
+    if world == 1 and not args.no_fp64_arm and prec != B.TN_PREC_FP64:
+        B.tn_contract_approx(ctx, plans, ptrs, B.TN_PREC_FP64, 0, sh)
+        B.tn_logz(ctx, Bn)
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        B.tn_contract_approx(ctx, plans, ptrs, B.TN_PREC_FP64, 0, sh)
+        e1.record(stream)
+        e1.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        lz64, st64 = B.tn_logz(ctx, Bn)
+        fp64_arm = {"value": Bn / (ms64 / 1e3), "unit": "contractions/s", "ms_per_step": ms64,
+                    "steps": 1, "warmup": 1, "status_ok": int((st64 == 0).sum()),
+                    "max_rel_logz_diff_vs_mixed": float(np.max(np.abs(lz64 - logz) / np.abs(lz64)))}
 
     out = {
         "metric": "approx contractions/s", "value": value, "unit": "contractions/s",
@@ -403,6 +441,8 @@ def bench_ours(args):
         "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline,
         "density_matrix_contractions": dm_group, "clocks": clocks,
         "status_ok": int((status == 0).sum()),
+        "measured_peaks_tflops": {k: round(v, 2) for k, v in mp.items()},
+        "latency_batch1": lat, "fp64_arm": fp64_arm,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         d = run_oracle(0, args.size, args.chi, args.cpu_seconds)
@@ -415,11 +455,17 @@ def bench_ours(args):
                       f"({d['seconds']:.1f} s, FP64 numpy oracle, BLAS threads = cores)"}
         out["parity"] = {"instances": len(ref),
                          "max_rel_logz_err_vs_oracle": float(np.max(np.abs(got - ref) / np.abs(ref)))}
+        if fp64_arm is not None:
+            out["fp64_arm"]["max_rel_logz_err_vs_oracle"] = float(
+                np.max(np.abs(lz64[:len(ref)] - ref) / np.abs(ref)))
         if args.size == 32:
             ex = exact_logz_32(len(logz))
             out["parity"]["exact_instances"] = len(ex)
             out["parity"]["max_rel_logz_err_vs_exact"] = float(
                 np.max(np.abs(logz[:len(ex)] - ex) / np.abs(ex)))
+            if fp64_arm is not None:
+                out["fp64_arm"]["max_rel_logz_err_vs_exact"] = float(
+                    np.max(np.abs(lz64[:len(ex)] - ex) / np.abs(ex)))
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -118,6 +118,12 @@ typedef struct {
   double flops_project;     /* projector application U_v^T M_v and the root    */
   double flops_eig;         /* eigensolver (Householder + back-transform)      */
   int64_t n_eig;            /* eigensolves per instance                        */
+  /* TN_PREC_TF32 (factored density matrices) replaces flops_density and
+   * flops_eig by these three:                                                */
+  double flops_factor;      /* Cholesky R_v = C_v C_v^T (D^3 / 3)              */
+  double flops_kfactor;     /* K_v = M_v C_v                                   */
+  double flops_svd;         /* Golub-Kahan bidiagonalisation of K_v + the
+                               back-transformation of the r_v kept vectors    */
 } tn_plan_info;
 
 /* ---------------------------------------------------------------- planning
@@ -331,6 +337,15 @@ tn_status tn_ctx_set_profiling(tn_ctx_t* ctx, int32_t on);
  * the ctx's stream, then resets the counters.  ms_host may be NULL.        */
 tn_status tn_ctx_profile(tn_ctx_t* ctx, double* ms_host, int64_t* launches_host,
                          int32_t n_classes);
+
+/* Arithmetic peaks of device (the paper has no counterpart: these are the
+ * roofline denominators of the kernels that are not bandwidth bound),
+ * measured by short burst kernels, best of three, TFLOP/s into tflops[0..3]
+ * (host): FP32 FMA, FP32 packed-pair FMA, FP64 FMA, and the tcgen05 tensor
+ * pipe in kind::tf32 (0 on devices other than sm_103).  Synchronous; takes
+ * well under a second; allocates and frees a few KB of device memory.
+ * TN_ERR_TIMEOUT if the tensor-pipe burst's bounded wait expired.          */
+tn_status tn_measure_peaks(int32_t device, double* tflops);
 
 /* One-line reason for the last non-OK status returned on this thread (ctx
  * may be NULL for calls that have none).  Valid until the next call.       */

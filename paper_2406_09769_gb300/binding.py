@@ -41,7 +41,9 @@ class tn_plan_info(ctypes.Structure):
                 ("max_eig_n", ctypes.c_int32), ("site_elems", ctypes.c_int64),
                 ("flops_env", ctypes.c_double), ("flops_local", ctypes.c_double),
                 ("flops_density", ctypes.c_double), ("flops_project", ctypes.c_double),
-                ("flops_eig", ctypes.c_double), ("n_eig", ctypes.c_int64)]
+                ("flops_eig", ctypes.c_double), ("n_eig", ctypes.c_int64),
+                ("flops_factor", ctypes.c_double), ("flops_kfactor", ctypes.c_double),
+                ("flops_svd", ctypes.c_double)]
 
 
 class TNError(RuntimeError):
@@ -58,7 +60,7 @@ EXPORTS = ("tn_plan", "tn_plan_destroy", "tn_plan_query", "tn_plan_site_offset",
            "tn_logz", "tn_contract_approx_host", "tn_embed_tree_noalloc",
            "tn_rank_model_params", "tn_rank_model_load", "tn_rank_record", "tn_rank_labels",
            "tn_rank_model_grad", "tn_rank_model_train",
-           "tn_ctx_set_profiling", "tn_ctx_profile", "tn_last_error")
+           "tn_ctx_set_profiling", "tn_ctx_profile", "tn_measure_peaks", "tn_last_error")
 
 KERNEL_CLASSES = ("norm", "fuse", "env", "local", "density", "eig", "project", "root", "close",
                   "factor")
@@ -103,6 +105,8 @@ def lib():
     L.tn_ctx_set_profiling.argtypes = [_vp, ctypes.c_int32]
     L.tn_ctx_profile.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]
+    L.tn_measure_peaks.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
+    L.tn_measure_peaks.restype = ctypes.c_int
     L.tn_last_error.argtypes = [_vp]
     L.tn_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -336,6 +340,16 @@ def tn_ctx_profile(ctx):
     cnt = (ctypes.c_int64 * n)()
     _check(lib().tn_ctx_profile(ctx.handle, ms, cnt, n), ctx)
     return {k: (int(cnt[i]), float(ms[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def tn_measure_peaks(device=0):
+    """Measured arithmetic peaks of the device in TFLOP/s: FP32 FMA, packed FP32x2
+    FMA, FP64 FMA and the tcgen05 tensor pipe in kind::tf32."""
+    out = (ctypes.c_double * 4)()
+    st = lib().tn_measure_peaks(int(device), out)
+    if st != 0:
+        raise TNError(st, f"tn_measure_peaks failed with status {st}")
+    return {"fp32": out[0], "fp32x2": out[1], "fp64": out[2], "tf32": out[3]}
 
 
 def pack_sites(plan, tensors):

@@ -364,6 +364,12 @@ void build(const tn_graph* g, const tn_plan_opts* o, tn_plan_t* P) {
       I.flops_density += 2.0 * A * Dr * Dr + 2.0 * A * A * Dr;
       I.flops_project += 2.0 * r * A * Dr;
       I.flops_eig += (4.0 / 3.0) * A * A * A + 4.0 * A * A * r;
+      // factored form: Cholesky of R_v, K_v = M_v C_v, bidiagonal SVD of K_v
+      I.flops_factor += Dr * Dr * Dr / 3.0;
+      I.flops_kfactor += 2.0 * A * Dr * Dr;
+      I.flops_svd += (A >= Dr ? 4.0 * A * Dr * Dr - (4.0 / 3.0) * Dr * Dr * Dr
+                              : 4.0 * Dr * A * A - (4.0 / 3.0) * A * A * A) +
+                     2.0 * A * A * r;
       I.max_eig_n = std::max(I.max_eig_n, int32_t(A));
       I.n_eig++;
     }
