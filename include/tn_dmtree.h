@@ -327,6 +327,21 @@ enum {
   TN_KC_FACTOR = 9,   /* Cholesky factors of the memoised environments       */
   TN_KC_COUNT = 10
 };
+/* Options of a ctx (the paper has no counterpart; they serve tuning and the
+ * tests of the failure paths):
+ *   TN_OPT_EIG_ROUNDS: multisection rounds of the TN_PREC_TF32 singular
+ *     value search after its shared grid round (1 .. 16, default 9, which
+ *     narrows every interval to ~4e-9 of ||T_GK||).  An interval still wider
+ *     than 128 eps_32 ||T_GK|| marks its instance TN_ERR_EIG_NOCONV.
+ *   TN_OPT_WAIT_PROBE: for the next tn_contract_approx only (value != 0),
+ *     every tensor-core contraction first waits, bounded (~2^14 polls), on
+ *     a device flag that nothing sets.  The expired wait takes the kernel's
+ *     error path (bounded drain of its copies in flight, tensor memory
+ *     released) and the batch reports TN_ERR_TIMEOUT from tn_logz; the ctx
+ *     stays usable.  It exercises the timeout handling without a fault.   */
+enum { TN_OPT_EIG_ROUNDS = 1, TN_OPT_WAIT_PROBE = 2 };
+tn_status tn_ctx_set_option(tn_ctx_t* ctx, int32_t option, int64_t value);
+
 /* Turn per-launch CUDA-event timing on (1) or off (0) for later batches of
  * ctx.  Launch counting is always on.  Timing adds two events per launch,
  * so timed numbers of a batch run with profiling on are diagnostics only. */

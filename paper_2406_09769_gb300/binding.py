@@ -60,7 +60,8 @@ EXPORTS = ("tn_plan", "tn_plan_destroy", "tn_plan_query", "tn_plan_site_offset",
            "tn_logz", "tn_contract_approx_host", "tn_embed_tree_noalloc",
            "tn_rank_model_params", "tn_rank_model_load", "tn_rank_record", "tn_rank_labels",
            "tn_rank_model_grad", "tn_rank_model_train",
-           "tn_ctx_set_profiling", "tn_ctx_profile", "tn_measure_peaks", "tn_last_error")
+           "tn_ctx_set_option", "tn_ctx_set_profiling", "tn_ctx_profile", "tn_measure_peaks",
+           "tn_last_error")
 
 KERNEL_CLASSES = ("norm", "fuse", "env", "local", "density", "eig", "project", "root", "close",
                   "factor")
@@ -102,6 +103,7 @@ def lib():
     L.tn_rank_model_grad.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int32, _vp, _vp, _vp, _vp]
     L.tn_rank_model_train.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.c_float, _vp, _vp, _vp]
+    L.tn_ctx_set_option.argtypes = [_vp, ctypes.c_int32, ctypes.c_int64]
     L.tn_ctx_set_profiling.argtypes = [_vp, ctypes.c_int32]
     L.tn_ctx_profile.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]
@@ -266,7 +268,9 @@ def tn_logz(ctx, n_inst, raise_on_error=False):
     status = np.empty(n_inst, dtype=np.int32)
     st = lib().tn_logz(ctx.handle, logz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                        status.ctypes.data_as(_i32p), int(n_inst))
-    if st != TN_OK and (raise_on_error or st not in (4, 5)):
+    # per-instance outcomes (non-finite, non-positive, timeout, no convergence)
+    # come back in status; anything else raises
+    if st != TN_OK and (raise_on_error or st not in (4, 5, 6, 7)):
         _check(st, ctx)
     return logz, status
 
@@ -282,7 +286,9 @@ def tn_contract_approx_host(ctx, plans, sites_host, precision=TN_PREC_FP64, lear
                                        int(learned_chi),
                                        logz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                        status.ctypes.data_as(_i32p), _vp(int(stream)))
-    if st != TN_OK and (raise_on_error or st not in (4, 5)):
+    # per-instance outcomes (non-finite, non-positive, timeout, no convergence)
+    # come back in status; anything else raises
+    if st != TN_OK and (raise_on_error or st not in (4, 5, 6, 7)):
         _check(st, ctx)
     return logz, status
 
@@ -340,6 +346,13 @@ def tn_ctx_profile(ctx):
     cnt = (ctypes.c_int64 * n)()
     _check(lib().tn_ctx_profile(ctx.handle, ms, cnt, n), ctx)
     return {k: (int(cnt[i]), float(ms[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+TN_OPT_EIG_ROUNDS, TN_OPT_WAIT_PROBE = 1, 2
+
+
+def tn_ctx_set_option(ctx, option, value):
+    _check(lib().tn_ctx_set_option(ctx.handle, int(option), int(value)), ctx)
 
 
 def tn_measure_peaks(device=0):

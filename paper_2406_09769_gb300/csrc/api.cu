@@ -104,6 +104,10 @@ struct tn_ctx {
   int* status = nullptr;
   double* logscale = nullptr;
   int* err_flag = nullptr;  // set by a kernel whose bounded wait expired
+  int* poll_flag = nullptr; // a device flag that nothing sets (TN_OPT_WAIT_PROBE)
+  // options (tn_ctx_set_option)
+  int eig_rounds = 9;       // SVD multisection rounds after the grid round
+  bool wait_probe = false;  // next batch: bounded wait on poll_flag in the GEMMs
 };
 
 namespace {
@@ -175,6 +179,7 @@ void ensure_results(tn_ctx* c, int B) {
   c->status = reinterpret_cast<int*>(base + 2 * align256(sizeof(double) * B));
   c->err_flag = reinterpret_cast<int*>(base + 2 * align256(sizeof(double) * B) +
                                        align256(sizeof(int) * B));
+  c->poll_flag = c->err_flag + 1;
 }
 
 // Per-step buffer offsets (elements) of one executor.
@@ -616,6 +621,7 @@ void tgemm(tn_ctx* c, int cls, const float* A, long long sA, int lda, const floa
   g.amax_out = amax_out; g.s_amax_out = s_out;
   g.split = split;
   g.err = c->err_flag;
+  g.poll = c->wait_probe ? c->poll_flag : nullptr;
   const bool aligned = (lda % 4 == 0) && (ldb % 4 == 0) && (sA % 4 == 0) && (sB % 4 == 0) &&
                        (reinterpret_cast<uintptr_t>(A) % 16 == 0) &&
                        (reinterpret_cast<uintptr_t>(Bm) % 16 == 0);
@@ -676,7 +682,7 @@ void dm_pass_tc(tn_ctx* c, const tn::Step& st, const Lay& l, const WsF& w, float
       // U_v = leading left singular vectors of K_v = leading eigenvectors of L_v
       Scope(c, TN_KC_EIG, strm),
       ck(tn::launch_svd_left(w.G, w.sM, A, Dr, Uk, w.sS, w.Ut, w.sUt, w.lam, w.sLam, rk,
-                             want_lam ? A : 0, c->status, B, strm),
+                             want_lam ? A : 0, c->status, B, strm, c->eig_rounds),
          "svd launch");
     } else {
       // L_v = M_v R_k M_v^T
@@ -714,7 +720,7 @@ void run_plan_tc(tn_ctx* c, const tn_plan_t* P, int B, const double* const* tens
   std::vector<Lay> lay;
   for (const tn::Step& st : P->steps) lay.push_back(lay_f32(st));
   ensure_results(c, B);
-  ck(cudaMemsetAsync(c->err_flag, 0, sizeof(int), strm), "memset err");
+  ck(cudaMemsetAsync(c->err_flag, 0, 2 * sizeof(int), strm), "memset err");
   const WsF w = carve_f32(c, P, lay, B);
   LearnState ls = learn_begin(c, P, B, learned, strm);
   const double** tens_table = nullptr;
@@ -775,6 +781,7 @@ void run_plan_tc(tn_ctx* c, const tn_plan_t* P, int B, const double* const* tens
   c->stream = strm;
   c->last_batch = B;
   c->pending = true;
+  c->wait_probe = false;
 }
 
 template <class F>
@@ -1354,6 +1361,23 @@ extern "C" tn_status tn_embed_tree_noalloc(int32_t n_inst, int32_t n_legs, const
                        cudaMemcpyDeviceToDevice, strm),
        "copy status");
     for (int k = 0; k < n - 1; ++k) ranks_host[k] = st.r[k];
+  });
+}
+
+extern "C" tn_status tn_ctx_set_option(tn_ctx_t* c, int32_t option, int64_t value) {
+  if (!c) {
+    tn::set_error("tn_ctx_set_option: ctx is NULL");
+    return TN_ERR_INVALID;
+  }
+  return guarded(c, "tn_ctx_set_option", [&] {
+    if (option == TN_OPT_EIG_ROUNDS) {
+      if (value < 1 || value > 16) fail(TN_ERR_INVALID, "TN_OPT_EIG_ROUNDS must be 1 .. 16");
+      c->eig_rounds = int(value);
+    } else if (option == TN_OPT_WAIT_PROBE) {
+      c->wait_probe = value != 0;
+    } else {
+      fail(TN_ERR_INVALID, "unknown option");
+    }
   });
 }
 

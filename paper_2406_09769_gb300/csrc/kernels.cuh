@@ -49,6 +49,7 @@ struct TcGemmArgs {
   int split;
   int ct_cols;   // C^T store groups columns n = q * ct_cols + c into Ct[c][m * (N / ct_cols) + q]
   int* err;
+  const int* poll;  // if set: a bounded wait on *poll != 0 first (expiry -> *err = 1)
 };
 cudaError_t tc_gemm_configure();
 cudaError_t launch_sgemm_nt(const TcGemmArgs& g, cudaStream_t st);
@@ -141,9 +142,12 @@ cudaError_t launch_iota(int* x, int n, cudaStream_t st);
 cudaError_t launch_chol_env(float* R, long long sR, const int64_t* r_off, const int32_t* D,
                             int maxD, const unsigned int* amax, long long s_amax, int k0, int nk,
                             int batch, cudaStream_t st);
+// rounds: multisection rounds after the shared grid round (1 .. 16; 9
+// resolve every interval to ~4e-9 ||T||); an interval left wider than 128
+// eps ||T|| marks the instance TN_ERR_EIG_NOCONV.
 cudaError_t launch_svd_left(const float* K, long long sK, int m, int n, float* U, long long sU,
                             float* Ut, long long sUt, double* lam, long long slam, int r,
-                            int nlam, int* status, int batch, cudaStream_t st);
+                            int nlam, int* status, int batch, cudaStream_t st, int rounds = 9);
 bool svd_left_supported(int m, int n, int r);
 size_t svd_left_smem_bytes(int m, int n, int r);
 cudaError_t svd_configure();

@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_svd_left(const float* __restric
                                                            float* __restrict__ Utg, long long sUt,
                                                            double* __restrict__ lamg,
                                                            long long slam, int r, int nlam,
-                                                           int* __restrict__ status) {
+                                                           int* __restrict__ status, int rounds) {
   extern __shared__ __align__(16) float sm[];
   const int p = m < n ? m : n;
   const int N = (m < n) ? 2 * p + 1 : 2 * p;
@@ -599,7 +599,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_svd_left(const float* __restric
       }
       float lo = (m0 > 0) ? fmaf(hg, float(m0), gl) : gl;
       float hi = (m0 < kThreads) ? fmaf(hg, float(m0 + 1), gl) : gu;
-      for (int it = 0; it < 9; ++it) {
+      for (int it = 0; it < rounds; ++it) {
         const float h = (hi - lo) / 5.f;
         const float x = fmaf(h, float(q + 1), lo);
         const int cnt = valid ? sturm_gk(e2, N, x, pivmin) : 0;
@@ -610,7 +610,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_svd_left(const float* __restric
         hi = (mm < 4) ? fmaf(h, float(mm + 1), lo) : hi;
         lo = nlo;
       }
-      if (valid && q == 0) lam[t] = fmaxf(0.5f * (lo + hi), 0.f);
+      if (valid && q == 0) {
+        lam[t] = fmaxf(0.5f * (lo + hi), 0.f);
+        if (hi - lo > 128.f * eps * tnorm) atomicCAS(status + b, 0, int(TN_ERR_EIG_NOCONV));
+      }
     }
   }
   __syncthreads();
@@ -837,11 +840,12 @@ bool svd_left_supported(int m, int n, int r) {
 
 cudaError_t launch_svd_left(const float* K, long long sK, int m, int n, float* U, long long sU,
                             float* Ut, long long sUt, double* lam, long long slam, int r,
-                            int nlam, int* status, int batch, cudaStream_t st) {
-  if (!svd_left_supported(m, n, r) || nlam < 0 || nlam > m) return cudaErrorInvalidValue;
+                            int nlam, int* status, int batch, cudaStream_t st, int rounds) {
+  if (!svd_left_supported(m, n, r) || nlam < 0 || nlam > m || rounds < 1 || rounds > 16)
+    return cudaErrorInvalidValue;
   const size_t smem = svd_left_smem_bytes(m, n, r);
   k_svd_left<<<batch, kThreads, smem, st>>>(K, sK, m, n, U, sU, Ut, sUt, lam, slam, r, nlam,
-                                            status);
+                                            status, rounds);
   return cudaGetLastError();
 }
 

@@ -41,6 +41,7 @@ constexpr int kLoBufs = 1;                    // lo halves of split chunks in fl
 constexpr uint32_t kEpiBytes = 8 * 32 * 33 * 4;  // per-warp 32 x 32 transpose tiles (padded)
 constexpr int kChunk = 32;                    // K elements per stage (128 bytes of FP32)
 constexpr uint32_t kWaitLimit = 1u << 22;     // bounded spin on every mbarrier
+constexpr uint32_t kPollLimit = 1u << 14;     // bounded poll of TcGemmArgs::poll
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -208,8 +209,19 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(const __grid_constant__ 
   if (tid == 0) {
     for (; issued < nk && issued < stages; ++issued) issue(issued);
   }
+  // A bounded wait on a device flag that nothing sets, when the caller asks
+  // for it: its expiry takes the same path as an expired mbarrier wait
+  // (error flag, drain of the TMA copies in flight, TMEM released).
+  if (tid == 0 && g.poll) {
+    bool seen = false;
+    for (uint32_t i = 0; i < kPollLimit && !seen; ++i)
+      seen = *reinterpret_cast<const volatile int*>(g.poll) != 0;
+    if (!seen) *abort_flag = 1;
+  }
+  __syncthreads();
+  const int nk_run = *abort_flag ? 0 : nk;
   int mma_chunks = 0;  // chunks whose MMAs thread 0 has issued
-  for (int kc = 0; kc < nk; ++kc) {
+  for (int kc = 0; kc < nk_run; ++kc) {
     const int s = kc % stages;
     const uint32_t ph = uint32_t(kc / stages) & 1u;
     unsigned char* st = base + s * tile_bytes;

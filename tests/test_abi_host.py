@@ -58,6 +58,7 @@ def _expected_flops(Lx, Ly, chi, q=2):
     d = [q] * Ly
     bond = [q] * (Ly - 1)            # boundary MPS after row 0 (horizontal bonds)
     env = local = dens = proj = 0.0
+    fac = kfac = svd = 0.0
     for _ in range(Lx - 2):
         D = [b * q for b in bond] + [1]
         r = [d[0]]
@@ -70,8 +71,15 @@ def _expected_flops(Lx, Ly, chi, q=2):
             local += 2.0 * r[k - 1] * D[k - 1] * d[k] * D[k]
             dens += 2.0 * A * D[k] ** 2 + 2.0 * A * A * D[k]
             proj += 2.0 * r[k] * A * D[k]
+            # factored form: Cholesky of R_k, K = M C, Golub-Kahan SVD of K
+            # (4 m n^2 - 4 n^3 / 3 with m >= n the longer side) + back-transform
+            fac += D[k] ** 3 / 3.0
+            kfac += 2.0 * A * D[k] ** 2
+            lo, hi = min(A, D[k]), max(A, D[k])
+            svd += 4.0 * hi * lo ** 2 - 4.0 * lo ** 3 / 3.0 + 2.0 * A * A * r[k]
         proj += 2.0 * r[Ly - 2] * D[Ly - 2] * d[Ly - 1]
         bond = r[:Ly - 1]
+    _expected_flops.factored = (fac, kfac, svd)
     return env, local, dens, proj
 
 
@@ -84,6 +92,17 @@ def test_plan_flops_match_cost_model(Lx, Ly, chi):
     assert info["flops_local"] == pytest.approx(local)
     assert info["flops_density"] == pytest.approx(dens)
     assert info["flops_project"] == pytest.approx(proj)
+    fac, kfac, svd = _expected_flops.factored
+    assert info["flops_factor"] == pytest.approx(fac)
+    assert info["flops_kfactor"] == pytest.approx(kfac)
+    assert info["flops_svd"] == pytest.approx(svd)
+
+
+def test_null_arguments_are_rejected_without_a_device():
+    lib = B.lib()
+    assert lib.tn_ctx_set_option(None, B.TN_OPT_EIG_ROUNDS, 9) == 1
+    assert lib.tn_measure_peaks(0, None) == 1
+    assert lib.tn_ctx_profile(None, None, None, 0) == 1
 
 
 @pytest.mark.parametrize("Lx,Ly,chi,q", [(6, 6, 12, 3), (5, 7, 20, 3), (4, 5, 16, 4)])
