@@ -177,9 +177,12 @@ tn_status tn_embed_tree(tn_ctx_t* ctx, int32_t n_inst, int32_t n_legs,
                         int32_t* status_dev, int32_t* ranks_host, void* stream);
 
 /* ------------------------------------------------------- whole contraction
- * Algorithm partitioned_contract for a batch of n_inst instances.  plans[i]
- * must be structurally identical (same graph shape, partition, path and
- * chi); instances differ in tensor data only.  sites_dev[i] is a device FP64
+ * Algorithm partitioned_contract for a batch of n_inst instances.  Plans may
+ * differ between instances (graph size, partition, path, chi): instances
+ * whose plans are structurally identical form a bucket that runs as one
+ * batch of launches; buckets run one after another on stream, with one
+ * upload of every bucket's tables and the workspace of the largest bucket.
+ * learned_chi = 1 needs a single bucket.  sites_dev[i] is a device FP64
  * buffer with every site tensor of instance i packed at tn_plan_site_offset.
  * Asynchronous on stream; results are read with tn_logz.  learned_chi = 0
  * keeps each edge's plan rank r_k; learned_chi = 1 lets the rank model of
@@ -189,19 +192,56 @@ tn_status tn_contract_approx(tn_ctx_t* ctx, const tn_plan_t* const* plans, int32
                              const double* const* sites_dev, int32_t precision,
                              int32_t learned_chi, void* stream);
 
-/* Waits for the last tn_contract_approx of ctx and copies its results to the
+/* Waits for the last tn_contract_approx of ctx and copies its results (in
+ * instance order, whatever the buckets) to the
  * host: logz_host[i] = ln Z of instance i (NaN if status != TN_OK) and
  * status_host[i] its tn_status.  Returns the first non-OK instance status.  */
 tn_status tn_logz(tn_ctx_t* ctx, double* logz_host, int32_t* status_host, int32_t n_inst);
 
 /* End-to-end form of tn_contract_approx + tn_logz from HOST site buffers:
- * copies sites_host[i] (host, FP64, packed as above; page-locked memory gives
- * asynchronous copies) to ctx-owned device memory, runs the batch and copies
- * ln Z and statuses back.  Synchronous.                                      */
+ * copies sites_host[i] (host, FP64, packed as above, plans[i]'s size;
+ * page-locked memory gives asynchronous copies) to ctx-owned device memory,
+ * runs the batch and copies ln Z and statuses back.  Synchronous.           */
 tn_status tn_contract_approx_host(tn_ctx_t* ctx, const tn_plan_t* const* plans, int32_t n_inst,
                                   const double* const* sites_host, int32_t precision,
                                   int32_t learned_chi, double* logz_host,
                                   int32_t* status_host, void* stream);
+
+/* ------------------------------------------------------ batching support
+ * The paper has no counterpart: these serve many-instance runs on one GPU.
+ *
+ * tn_autotune times, for every tensor-core contraction shape (M, N, K, split,
+ * batch) that the given batch launches, the tile widths 64 / 128 / 256 and the
+ * shared-memory budgets 70 / 104 / 200 KB of the tcgen05 kernel on the real
+ * operands (every candidate computes the same values: the tile width only
+ * partitions N, the K order is fixed) and keeps the fastest per shape in ctx;
+ * later batches of ctx use it.  Synchronous; runs the batch once per
+ * candidate of each shape (its results are discarded).  cache_path (host
+ * string, may be NULL): a JSON file written for this device is loaded instead
+ * of tuning; otherwise the table is written there.  No-op for TN_PREC_FP64.
+ * tn_autotune_entries reports the number of tuned shapes.
+ *
+ * tn_batch_graph_capture records one whole batch (the arguments of
+ * tn_contract_approx without learned ranks) into a CUDA graph that owns a
+ * private workspace: it runs the batch once to size the workspace and place
+ * the tables, then captures the same launches.  The graph reads the site
+ * buffers at the given device addresses on every replay: keep them alive and
+ * at the same addresses (their contents may change between replays).
+ * ctx's options and autotuned tiles are copied at capture.
+ * tn_batch_graph_launch replays it on stream (asynchronous);
+ * tn_batch_graph_logz waits for the last replay and copies ln Z and statuses
+ * to the host as tn_logz does.                                             */
+typedef struct tn_batch_graph tn_batch_graph_t;
+tn_status tn_autotune(tn_ctx_t* ctx, const tn_plan_t* const* plans, int32_t n_inst,
+                      const double* const* sites_dev, int32_t precision, const char* cache_path);
+tn_status tn_autotune_entries(const tn_ctx_t* ctx, int32_t* n_entries);
+tn_status tn_batch_graph_capture(tn_ctx_t* ctx, const tn_plan_t* const* plans, int32_t n_inst,
+                                 const double* const* sites_dev, int32_t precision,
+                                 tn_batch_graph_t** out);
+tn_status tn_batch_graph_launch(tn_batch_graph_t* graph, void* stream);
+tn_status tn_batch_graph_logz(tn_batch_graph_t* graph, double* logz_host, int32_t* status_host,
+                              int32_t n_inst);
+tn_status tn_batch_graph_destroy(tn_batch_graph_t* graph);
 
 /* ------------------------------------------------ allocation-free variant
  * The paper has no counterpart: this entry point exists for callers of this

@@ -61,7 +61,8 @@ EXPORTS = ("tn_plan", "tn_plan_destroy", "tn_plan_query", "tn_plan_site_offset",
            "tn_rank_model_params", "tn_rank_model_load", "tn_rank_record", "tn_rank_labels",
            "tn_rank_model_grad", "tn_rank_model_train",
            "tn_ctx_set_option", "tn_ctx_set_profiling", "tn_ctx_profile", "tn_measure_peaks",
-           "tn_last_error")
+           "tn_autotune", "tn_autotune_entries", "tn_batch_graph_capture", "tn_batch_graph_launch",
+           "tn_batch_graph_logz", "tn_batch_graph_destroy", "tn_last_error")
 
 KERNEL_CLASSES = ("norm", "fuse", "env", "local", "density", "eig", "project", "root", "close",
                   "factor")
@@ -104,6 +105,14 @@ def lib():
     L.tn_rank_model_train.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.c_float, _vp, _vp, _vp]
     L.tn_ctx_set_option.argtypes = [_vp, ctypes.c_int32, ctypes.c_int64]
+    L.tn_autotune.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.c_int32, ctypes.POINTER(_vp),
+                              ctypes.c_int32, ctypes.c_char_p]
+    L.tn_autotune_entries.argtypes = [_vp, _i32p]
+    L.tn_batch_graph_capture.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.c_int32, ctypes.POINTER(_vp),
+                                   ctypes.c_int32, ctypes.POINTER(_vp)]
+    L.tn_batch_graph_launch.argtypes = [_vp, _vp]
+    L.tn_batch_graph_logz.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), _i32p, ctypes.c_int32]
+    L.tn_batch_graph_destroy.argtypes = [_vp]
     L.tn_ctx_set_profiling.argtypes = [_vp, ctypes.c_int32]
     L.tn_ctx_profile.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]
@@ -349,6 +358,46 @@ def tn_ctx_profile(ctx):
 
 
 TN_OPT_EIG_ROUNDS, TN_OPT_WAIT_PROBE = 1, 2
+
+
+def tn_autotune(ctx, plans, sites_dev, precision=TN_PREC_TF32, cache_path=None):
+    """Tune the tensor-core tiles of ctx on this batch (or load cache_path)."""
+    hs = _ptrs([p.handle.value for p in plans])
+    cp = cache_path.encode() if cache_path else None
+    _check(lib().tn_autotune(ctx.handle, hs, len(plans), _ptrs(sites_dev), int(precision), cp),
+           ctx)
+    n = ctypes.c_int32()
+    _check(lib().tn_autotune_entries(ctx.handle, ctypes.byref(n)), ctx)
+    return n.value
+
+
+class Graph:
+    """A captured batch (tn_batch_graph_capture); replay with launch(), read with logz()."""
+
+    def __init__(self, ctx, plans, sites_dev, precision=TN_PREC_TF32):
+        self.handle = _vp()
+        self.n = len(plans)
+        self._plans = plans  # the graph reads the plans' tables only at capture
+        hs = _ptrs([p.handle.value for p in plans])
+        _check(lib().tn_batch_graph_capture(ctx.handle, hs, len(plans), _ptrs(sites_dev),
+                                      int(precision), ctypes.byref(self.handle)), ctx)
+
+    def launch(self, stream=0):
+        _check(lib().tn_batch_graph_launch(self.handle, _vp(stream)))
+
+    def logz(self):
+        logz = np.empty(self.n, dtype=np.float64)
+        status = np.empty(self.n, dtype=np.int32)
+        st = lib().tn_batch_graph_logz(self.handle, logz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 status.ctypes.data_as(_i32p), self.n)
+        if st != TN_OK and st not in (4, 5, 6, 7):
+            _check(st)
+        return logz, status
+
+    def __del__(self):
+        if getattr(self, "handle", None) and self.handle.value and _lib is not None:
+            _lib.tn_batch_graph_destroy(self.handle)
+            self.handle = _vp()
 
 
 def tn_ctx_set_option(ctx, option, value):

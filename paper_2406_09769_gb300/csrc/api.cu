@@ -3,10 +3,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -108,6 +110,12 @@ struct tn_ctx {
   // options (tn_ctx_set_option)
   int eig_rounds = 9;       // SVD multisection rounds after the grid round
   bool wait_probe = false;  // next batch: bounded wait on poll_flag in the GEMMs
+  // result slot of each instance of the last batch (bucketed batches)
+  std::vector<int> slot;
+  bool slot_identity = true;
+  // autotuned tensor-core tiles: {M, N, K, split, batch} -> {tile width, smem budget KB}
+  std::map<std::array<int, 5>, std::array<int, 3>> tune;  // value: BN, budget KB, time (ns)
+  bool tuning = false;
 };
 
 namespace {
@@ -150,7 +158,9 @@ Dims plan_dims(const tn_plan_t* P) {
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-Ws carve(tn_ctx* c, const Dims& d, int B, int nv) {
+// bytes: if set, receives the workspace size; with dry = true nothing is
+// allocated and the returned pointers are not valid.
+Ws carve(tn_ctx* c, const Dims& d, int B, int nv, bool dry = false, size_t* bytes = nullptr) {
   Ws w{};
   w.sS = d.maxS; w.sY = d.maxY; w.sR = d.maxR; w.sX = d.maxX; w.sM = d.maxM;
   w.sL = d.maxL; w.sP = d.maxP; w.sLam = d.maxLam; w.sAmax = d.maxN; w.sInv = nv;
@@ -164,6 +174,8 @@ Ws carve(tn_ctx* c, const Dims& d, int B, int nv) {
   }
   off[11] = tot;
   tot += align256(sizeof(unsigned long long) * size_t(w.sAmax) * B);
+  if (bytes) *bytes = tot;
+  if (dry) return w;
   char* base = static_cast<char*>(c->arena.get(tot));
   double** outs[] = {&w.S0, &w.S1, &w.Y, &w.R, &w.X, &w.M, &w.G, &w.L, &w.P, &w.lam, &w.inv};
   for (int i = 0; i < 11; ++i) *outs[i] = reinterpret_cast<double*>(base + off[i]);
@@ -274,67 +286,90 @@ struct StepTables {
   int64_t* r_off;  // memoised density matrix R_k offsets (n entries)
 };
 
-std::vector<StepTables> upload_tables(tn_ctx* c, const tn_plan_t* P, const std::vector<Lay>& lay,
-                                      const double* const* tens_dev, int B,
-                                      const double*** tens_table, int64_t** off_dev,
-                                      int64_t** len_dev, cudaStream_t st) {
-  // layout: [tens ptrs B][site_off nv][site_len nv] then per step fuse/y_off/D
+// Device copies of one bucket's per-step tables: [tens ptrs B][site_off nv]
+// [site_len nv] then per step fuse / y_off / D / r_off.
+size_t tables_bytes(const tn_plan_t* P, int B) {
   const int nv = P->n_vertices;
   size_t tot = align256(sizeof(void*) * B) + 2 * align256(sizeof(int64_t) * nv);
-  std::vector<size_t> so(P->steps.size());
   for (size_t s = 0; s < P->steps.size(); ++s) {
-    so[s] = tot;
     const int n = P->steps[s].n;
     tot += align256(sizeof(tn::FuseSite) * n) + 2 * align256(sizeof(int64_t) * n) +
            align256(sizeof(int32_t) * (n + 1));
   }
-  char* h = static_cast<char*>(pinned_get(c, tot));
-  char* dbase = static_cast<char*>(c->tables.get(tot));
-  std::memcpy(h, tens_dev, sizeof(void*) * B);
+  return tot;
+}
+
+// Lays out the tables at device address dbase; writes their host image at h
+// when h is not NULL (h == NULL: the device copy is already in place).
+std::vector<StepTables> fill_tables(const tn_plan_t* P, const std::vector<Lay>& lay,
+                                    const double* const* tens_dev, int B, char* h, char* dbase,
+                                    const double*** tens_table, int64_t** off_dev,
+                                    int64_t** len_dev) {
+  const int nv = P->n_vertices;
   size_t o = align256(sizeof(void*) * B);
-  std::memcpy(h + o, P->site_off.data(), sizeof(int64_t) * nv);
+  if (h) std::memcpy(h, tens_dev, sizeof(void*) * B);
+  if (h) std::memcpy(h + o, P->site_off.data(), sizeof(int64_t) * nv);
   *off_dev = reinterpret_cast<int64_t*>(dbase + o);
   o += align256(sizeof(int64_t) * nv);
-  std::memcpy(h + o, P->site_len.data(), sizeof(int64_t) * nv);
+  if (h) std::memcpy(h + o, P->site_len.data(), sizeof(int64_t) * nv);
   *len_dev = reinterpret_cast<int64_t*>(dbase + o);
+  o += align256(sizeof(int64_t) * nv);
   *tens_table = reinterpret_cast<const double**>(dbase);
   std::vector<StepTables> out(P->steps.size());
   for (size_t s = 0; s < P->steps.size(); ++s) {
     const tn::Step& stp = P->steps[s];
     const int n = stp.n;
-    size_t q = so[s];
-    tn::FuseSite* fh = reinterpret_cast<tn::FuseSite*>(h + q);
+    size_t q = o;
     out[s].fuse = reinterpret_cast<tn::FuseSite*>(dbase + q);
-    for (int k = 0; k < n; ++k) {
-      const tn::SiteOp& op = stp.site[k];
-      tn::FuseSite f{};
-      f.vertex = op.vertex; f.a = op.a; f.dp = op.dp; f.b = op.b;
-      f.dhl = op.dhl; f.dhr = op.dhr; f.de = op.de;
-      f.t_off = op.t_off; f.sp = op.sp; f.shl = op.shl; f.shr = op.shr; f.se = op.se;
-      f.y_off = (stp.kind == 0) ? lay[s].s_off[k] : lay[s].y_off[k];
-      f.s_off = (s > 0) ? lay[s - 1].s_off[k] : 0;
-      fh[k] = f;
+    if (h) {
+      tn::FuseSite* fh = reinterpret_cast<tn::FuseSite*>(h + q);
+      for (int k = 0; k < n; ++k) {
+        const tn::SiteOp& op = stp.site[k];
+        tn::FuseSite f{};
+        f.vertex = op.vertex; f.a = op.a; f.dp = op.dp; f.b = op.b;
+        f.dhl = op.dhl; f.dhr = op.dhr; f.de = op.de;
+        f.t_off = op.t_off; f.sp = op.sp; f.shl = op.shl; f.shr = op.shr; f.se = op.se;
+        f.y_off = (stp.kind == 0) ? lay[s].s_off[k] : lay[s].y_off[k];
+        f.s_off = (s > 0) ? lay[s - 1].s_off[k] : 0;
+        fh[k] = f;
+      }
     }
     q += align256(sizeof(tn::FuseSite) * n);
-    std::memcpy(h + q, lay[s].y_off.data(), sizeof(int64_t) * n);
+    if (h) std::memcpy(h + q, lay[s].y_off.data(), sizeof(int64_t) * n);
     out[s].y_off = reinterpret_cast<int64_t*>(dbase + q);
     q += align256(sizeof(int64_t) * n);
-    std::vector<int32_t> D(stp.D);
-    int mx = 1;
-    for (int x : D) mx = std::max(mx, x);
-    D.push_back(mx);
-    std::memcpy(h + q, D.data(), sizeof(int32_t) * (n + 1));
+    if (h) {
+      std::vector<int32_t> D(stp.D);
+      int mx = 1;
+      for (int x : D) mx = std::max(mx, x);
+      D.push_back(mx);
+      std::memcpy(h + q, D.data(), sizeof(int32_t) * (n + 1));
+    }
     out[s].D = reinterpret_cast<int32_t*>(dbase + q);
     q += align256(sizeof(int32_t) * (n + 1));
-    std::vector<int64_t> ro(lay[s].r_off);
-    ro.resize(n, 0);
-    std::memcpy(h + q, ro.data(), sizeof(int64_t) * n);
+    if (h) {
+      std::vector<int64_t> ro(lay[s].r_off);
+      ro.resize(n, 0);
+      std::memcpy(h + q, ro.data(), sizeof(int64_t) * n);
+    }
     out[s].r_off = reinterpret_cast<int64_t*>(dbase + q);
+    q += align256(sizeof(int64_t) * n);
+    o = q;
   }
-  ck(cudaMemcpyAsync(dbase, h, tot, cudaMemcpyHostToDevice, st), "upload tables");
-  ck(cudaEventRecord(c->pinned_free, st), "cudaEventRecord");
   return out;
 }
+
+// One bucket of a batch: instances whose plans are structurally equal.
+struct Bucket {
+  const tn_plan_t* P = nullptr;
+  std::vector<int> idx;                // instances of the batch, in order
+  std::vector<const double*> sites;    // their site buffers
+  std::vector<Lay> lay;
+  size_t ws_bytes = 0, tab_off = 0, res_off = 0;
+  std::vector<StepTables> tabs;
+  const double** tens_table = nullptr;
+  int64_t *off_dev = nullptr, *len_dev = nullptr;
+};
 
 void gemm(tn_ctx* c, int cls, bool ta, bool tb, const double* A, long long sA, int lda,
           const double* Bm, long long sB, int ldb, double* C, long long sC, int ldc, int M, int N,
@@ -486,19 +521,17 @@ void dm_pass(tn_ctx* c, const tn::Step& st, const Ws& w, double* Snext, int B, i
      "root launch");
 }
 
-void run_plan(tn_ctx* c, const tn_plan_t* P, int B, const double* const* tens_dev, int precision,
-              bool learned, cudaStream_t strm) {
+// FP64 path of one bucket (tables in place, results at c->logz etc.).
+void run_plan(tn_ctx* c, const Bucket& bk, int precision, bool learned, cudaStream_t strm) {
+  const tn_plan_t* P = bk.P;
+  const int B = int(bk.idx.size());
   const Dims dm = plan_dims(P);
-  ensure_results(c, B);
-  ck(cudaMemsetAsync(c->err_flag, 0, sizeof(int), strm), "memset err");
   LearnState ls = learn_begin(c, P, B, learned, strm);
   const Ws w = carve(c, dm, B, P->n_vertices);
-  const double** tens_table = nullptr;
-  int64_t *off_dev = nullptr, *len_dev = nullptr;
-  std::vector<Lay> lay;
-  for (const tn::Step& st : P->steps) lay.push_back(lay_fp64(st));
-  std::vector<StepTables> tabs =
-      upload_tables(c, P, lay, tens_dev, B, &tens_table, &off_dev, &len_dev, strm);
+  const double** tens_table = bk.tens_table;
+  const int64_t* off_dev = bk.off_dev;
+  const int64_t* len_dev = bk.len_dev;
+  const std::vector<StepTables>& tabs = bk.tabs;
   Scope(c, TN_KC_NORM, strm),
   ck(tn::launch_site_norm(tens_table, off_dev, len_dev, P->n_vertices, B, w.inv, c->logscale,
                           c->status, strm),
@@ -539,9 +572,6 @@ void run_plan(tn_ctx* c, const tn_plan_t* P, int B, const double* const* tens_de
          "close");
     }
   }
-  c->stream = strm;
-  c->last_batch = B;
-  c->pending = true;
 }
 
 // ------------------------------------------------------ mixed precision path
@@ -556,7 +586,8 @@ struct WsF {
   unsigned int* amax;
 };
 
-WsF carve_f32(tn_ctx* c, const tn_plan_t* P, const std::vector<Lay>& lay, int B) {
+WsF carve_f32(tn_ctx* c, const tn_plan_t* P, const std::vector<Lay>& lay, int B,
+              bool dry = false, size_t* bytes = nullptr) {
   long long maxS = 4, maxY = 4, maxR = 4, maxX = 4, maxM = 4, maxL = 4, maxP = 4, maxUt = 4,
             maxLam = 1;
   int maxN = 1;
@@ -596,6 +627,8 @@ WsF carve_f32(tn_ctx* c, const tn_plan_t* P, const std::vector<Lay>& lay, int B)
   tot += align256(sizeof(double) * size_t(w.sInv) * B);
   off[14] = tot;
   tot += align256(sizeof(unsigned int) * size_t(w.sAmax) * B);
+  if (bytes) *bytes = tot;
+  if (dry) return w;
   char* base = static_cast<char*>(c->arena.get(tot));
   for (int i = 0; i < 12; ++i) *fout[i] = reinterpret_cast<float*>(base + off[i]);
   w.lam = reinterpret_cast<double*>(base + off[12]);
@@ -626,6 +659,50 @@ void tgemm(tn_ctx* c, int cls, const float* A, long long sA, int lda, const floa
                        (reinterpret_cast<uintptr_t>(A) % 16 == 0) &&
                        (reinterpret_cast<uintptr_t>(Bm) % 16 == 0);
   if (aligned && c->tc_ready) {
+    const std::array<int, 5> key{M, N, K, split, batch};
+    if (c->tuning) {
+      // time every candidate tile width and shared-memory budget once on the
+      // real operands (all compute the same values: BN only partitions N and
+      // the K order is fixed) and keep the fastest; the last run's output
+      // stands
+      std::vector<std::array<int, 2>> cand;
+      const int nr = std::min(256, ((N + 15) / 16) * 16);
+      for (int bn : {64, 128, 256}) {
+        if (bn > std::max(64, nr)) continue;
+        const int b = std::min(bn, nr);
+        for (int kb : {70, 104, 200}) cand.push_back({b, kb});
+      }
+      cudaEvent_t e0, e1;
+      ck(cudaEventCreate(&e0), "cudaEventCreate");
+      ck(cudaEventCreate(&e1), "cudaEventCreate");
+      std::array<int, 3> best{0, 0, 0};
+      float best_ms = 1e30f;
+      for (const auto& cd : cand) {
+        g.bn = cd[0];
+        g.budget_kb = cd[1];
+        ck(cudaEventRecord(e0, st), "cudaEventRecord");
+        ck(tn::launch_tc_gemm(g, st), "tcgen05 gemm launch");
+        ck(cudaEventRecord(e1, st), "cudaEventRecord");
+        ck(cudaEventSynchronize(e1), "cudaEventSynchronize");
+        float ms = 0.f;
+        ck(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = {cd[0], cd[1], int(ms * 1e6f)};
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      c->tune[key] = best;
+      g.bn = best[0];
+      g.budget_kb = best[1];
+    } else {
+      const auto it = c->tune.find(key);
+      if (it != c->tune.end()) {
+        g.bn = it->second[0];
+        g.budget_kb = it->second[1];
+      }
+    }
     ck(tn::launch_tc_gemm(g, st), "tcgen05 gemm launch");
   } else {
     ck(tn::launch_sgemm_nt(g, st), "sgemm launch");
@@ -707,26 +784,18 @@ void dm_pass_tc(tn_ctx* c, const tn::Step& st, const Lay& l, const WsF& w, float
      "root launch");
 }
 
-void run_plan_tc(tn_ctx* c, const tn_plan_t* P, int B, const double* const* tens_dev,
-                 int sub_split, bool factored, bool learned, cudaStream_t strm) {
-  if (factored)
-    for (const tn::Step& st : P->steps) {
-      if (st.kind != 1) continue;
-      for (int k = 1; k <= st.n - 2; ++k)
-        if (!tn::svd_left_supported(st.r[k - 1] * st.d[k], st.D[k], st.r[k]))
-          fail(TN_ERR_UNSUPPORTED,
-               "TN_PREC_TF32 needs dim A_v <= 128, tree-edge dims <= 128 and ranks <= 64");
-    }
-  std::vector<Lay> lay;
-  for (const tn::Step& st : P->steps) lay.push_back(lay_f32(st));
-  ensure_results(c, B);
-  ck(cudaMemsetAsync(c->err_flag, 0, 2 * sizeof(int), strm), "memset err");
+// Mixed path of one bucket (tables in place, results at c->logz etc.).
+void run_plan_tc(tn_ctx* c, const Bucket& bk, int sub_split, bool factored, bool learned,
+                 cudaStream_t strm) {
+  const tn_plan_t* P = bk.P;
+  const int B = int(bk.idx.size());
+  const std::vector<Lay>& lay = bk.lay;
   const WsF w = carve_f32(c, P, lay, B);
   LearnState ls = learn_begin(c, P, B, learned, strm);
-  const double** tens_table = nullptr;
-  int64_t *off_dev = nullptr, *len_dev = nullptr;
-  std::vector<StepTables> tabs =
-      upload_tables(c, P, lay, tens_dev, B, &tens_table, &off_dev, &len_dev, strm);
+  const double** tens_table = bk.tens_table;
+  const int64_t* off_dev = bk.off_dev;
+  const int64_t* len_dev = bk.len_dev;
+  const std::vector<StepTables>& tabs = bk.tabs;
   Scope(c, TN_KC_NORM, strm),
   ck(tn::launch_site_norm(tens_table, off_dev, len_dev, P->n_vertices, B, w.inv, c->logscale,
                           c->status, strm),
@@ -778,8 +847,106 @@ void run_plan_tc(tn_ctx* c, const tn_plan_t* P, int B, const double* const* tens
          "close");
     }
   }
+}
+
+// Restores the ctx's result pointers after a bucketed batch (also on error).
+struct ResultView {
+  tn_ctx* c;
+  double *logz, *logscale;
+  int* status;
+  explicit ResultView(tn_ctx* c_) : c(c_), logz(c_->logz), logscale(c_->logscale), status(c_->status) {}
+  void at(size_t off) {
+    c->logz = logz + off;
+    c->logscale = logscale + off;
+    c->status = status + off;
+  }
+  ~ResultView() {
+    c->logz = logz;
+    c->logscale = logscale;
+    c->status = status;
+  }
+};
+
+// Algorithm partitioned_contract for a batch whose instances may have
+// different plans (sizes, chi): instances with structurally equal plans form
+// a bucket; all buckets' tables go to the device in one copy, the workspace
+// is sized for the largest bucket and reused by the next (stream order), and
+// each bucket writes its slice of the results.  upload = false leaves the
+// tables as a previous identical call placed them (graph capture).
+void run_batch(tn_ctx* c, const tn_plan_t* const* plans, int n, const double* const* sites,
+               int precision, bool learned, cudaStream_t strm, bool upload) {
+  const bool tc = precision != TN_PREC_FP64;
+  const int sub_split = (precision == TN_PREC_TF32_FAST) ? 0 : 1;
+  const bool factored = precision == TN_PREC_TF32;
+  std::vector<Bucket> bks;
+  for (int i = 0; i < n; ++i) {
+    size_t b = bks.size();
+    for (size_t j = 0; j < bks.size(); ++j)
+      if (tn::plans_equivalent(bks[j].P, plans[i])) {
+        b = j;
+        break;
+      }
+    if (b == bks.size()) {
+      bks.emplace_back();
+      bks.back().P = plans[i];
+    }
+    bks[b].idx.push_back(i);
+    bks[b].sites.push_back(sites[i]);
+  }
+  if (learned && bks.size() > 1)
+    fail(TN_ERR_UNSUPPORTED, "learned ranks need one plan structure per batch");
+  if (factored)
+    for (const Bucket& bk : bks)
+      for (const tn::Step& st : bk.P->steps) {
+        if (st.kind != 1) continue;
+        for (int k = 1; k <= st.n - 2; ++k)
+          if (!tn::svd_left_supported(st.r[k - 1] * st.d[k], st.D[k], st.r[k]))
+            fail(TN_ERR_UNSUPPORTED,
+                 "TN_PREC_TF32 needs dim A_v <= 128, tree-edge dims <= 128 and ranks <= 64");
+      }
+  size_t ws_max = 0, tab_tot = 0, res = 0;
+  std::vector<int> slot(n, 0);
+  for (Bucket& bk : bks) {
+    const int B = int(bk.idx.size());
+    for (const tn::Step& st : bk.P->steps) bk.lay.push_back(tc ? lay_f32(st) : lay_fp64(st));
+    if (tc)
+      carve_f32(c, bk.P, bk.lay, B, true, &bk.ws_bytes);
+    else
+      carve(c, plan_dims(bk.P), B, bk.P->n_vertices, true, &bk.ws_bytes);
+    ws_max = std::max(ws_max, bk.ws_bytes);
+    bk.tab_off = tab_tot;
+    tab_tot += align256(tables_bytes(bk.P, B));
+    bk.res_off = res;
+    for (int k = 0; k < B; ++k) slot[bk.idx[k]] = int(res) + k;
+    res += B;
+  }
+  ensure_results(c, n);
+  c->arena.get(ws_max);
+  char* dbase = static_cast<char*>(c->tables.get(tab_tot));
+  char* h = upload ? static_cast<char*>(pinned_get(c, tab_tot)) : nullptr;
+  for (Bucket& bk : bks)
+    bk.tabs = fill_tables(bk.P, bk.lay, bk.sites.data(), int(bk.idx.size()),
+                          h ? h + bk.tab_off : nullptr, dbase + bk.tab_off, &bk.tens_table,
+                          &bk.off_dev, &bk.len_dev);
+  if (upload) {
+    ck(cudaMemcpyAsync(dbase, h, tab_tot, cudaMemcpyHostToDevice, strm), "upload tables");
+    ck(cudaEventRecord(c->pinned_free, strm), "cudaEventRecord");
+  }
+  ck(cudaMemsetAsync(c->err_flag, 0, 2 * sizeof(int), strm), "memset err");
+  {
+    ResultView view(c);
+    for (const Bucket& bk : bks) {
+      view.at(bk.res_off);
+      if (tc)
+        run_plan_tc(c, bk, sub_split, factored, learned, strm);
+      else
+        run_plan(c, bk, precision, learned, strm);
+    }
+  }
+  c->slot = std::move(slot);
+  c->slot_identity = bks.size() == 1;
   c->stream = strm;
-  c->last_batch = B;
+  c->last_batch = n;
   c->pending = true;
   c->wait_probe = false;
 }
@@ -872,23 +1039,17 @@ extern "C" tn_status tn_contract_approx(tn_ctx_t* c, const tn_plan_t* const* pla
     if (!plans || !sites_dev || n_inst < 1) fail(TN_ERR_INVALID, "plans/sites NULL or n_inst < 1");
     if (learned_chi && !c->have_model)
       fail(TN_ERR_INVALID, "learned_chi = 1 needs a rank model (tn_rank_model_load)");
-    for (int i = 0; i < n_inst; ++i) {
+    for (int i = 0; i < n_inst; ++i)
       if (!plans[i] || !sites_dev[i]) fail(TN_ERR_INVALID, "NULL plan or site buffer");
-      if (!tn::plans_equivalent(plans[0], plans[i]))
-        fail(TN_ERR_UNSUPPORTED, "instances of one batch must share the plan structure");
-    }
     ck(cudaSetDevice(c->device), "cudaSetDevice");
     cudaStream_t strm = static_cast<cudaStream_t>(stream);
-    if (precision == TN_PREC_FP64) {
-      run_plan(c, plans[0], n_inst, sites_dev, precision, learned_chi != 0, strm);
-    } else if (precision == TN_PREC_TF32 || precision == TN_PREC_TF32_FAST ||
-               precision == TN_PREC_TF32_GRAM) {
+    if (precision == TN_PREC_TF32 || precision == TN_PREC_TF32_FAST ||
+        precision == TN_PREC_TF32_GRAM) {
       if (!c->tc_ready) fail(TN_ERR_UNSUPPORTED, "tcgen05 path unavailable on this device");
-      run_plan_tc(c, plans[0], n_inst, sites_dev, precision == TN_PREC_TF32_FAST ? 0 : 1,
-                  precision == TN_PREC_TF32, learned_chi != 0, strm);
-    } else {
+    } else if (precision != TN_PREC_FP64) {
       fail(TN_ERR_UNSUPPORTED, "precision mode not implemented in this build");
     }
+    run_batch(c, plans, n_inst, sites_dev, precision, learned_chi != 0, strm, true);
   });
 }
 
@@ -1038,16 +1199,28 @@ extern "C" tn_status tn_logz(tn_ctx_t* c, double* logz_host, int32_t* status_hos
     if (n_inst != c->last_batch) fail(TN_ERR_INVALID, "n_inst differs from the launched batch");
     if (!logz_host || !status_host) fail(TN_ERR_INVALID, "NULL output");
     ck(cudaSetDevice(c->device), "cudaSetDevice");
-    ck(cudaMemcpyAsync(logz_host, c->logz, sizeof(double) * n_inst, cudaMemcpyDeviceToHost,
+    // bucketed batches keep results in slot order: copy, then put back in
+    // instance order
+    const bool ident = c->slot_identity || int(c->slot.size()) != n_inst;
+    std::vector<double> lz(ident ? 0 : n_inst);
+    std::vector<int> stt(ident ? 0 : n_inst);
+    double* lz_dst = ident ? logz_host : lz.data();
+    int* st_dst = ident ? status_host : stt.data();
+    ck(cudaMemcpyAsync(lz_dst, c->logz, sizeof(double) * n_inst, cudaMemcpyDeviceToHost,
                        c->stream),
        "copy logz");
-    ck(cudaMemcpyAsync(status_host, c->status, sizeof(int) * n_inst, cudaMemcpyDeviceToHost,
+    ck(cudaMemcpyAsync(st_dst, c->status, sizeof(int) * n_inst, cudaMemcpyDeviceToHost,
                        c->stream),
        "copy status");
     int err = 0;
     ck(cudaMemcpyAsync(&err, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
        "copy err");
     ck(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    if (!ident)
+      for (int i = 0; i < n_inst; ++i) {
+        logz_host[i] = lz[c->slot[i]];
+        status_host[i] = stt[c->slot[i]];
+      }
     if (err) {
       for (int i = 0; i < n_inst; ++i) {
         status_host[i] = TN_ERR_TIMEOUT;
@@ -1078,15 +1251,19 @@ extern "C" tn_status tn_contract_approx_host(tn_ctx_t* c, const tn_plan_t* const
       fail(TN_ERR_INVALID, "plans/sites NULL or n_inst < 1");
     ck(cudaSetDevice(c->device), "cudaSetDevice");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int64_t per = plans[0]->site_elems;
-    double* dev = static_cast<double*>(c->stage.get(sizeof(double) * size_t(per) * n_inst));
+    // each instance's site buffer at its own offset (plans may differ)
+    std::vector<int64_t> off(n_inst + 1, 0);
+    for (int i = 0; i < n_inst; ++i) {
+      if (!plans[i] || !sites_host[i]) fail(TN_ERR_INVALID, "NULL plan or site buffer");
+      off[i + 1] = off[i] + ((plans[i]->site_elems + 31) & ~int64_t(31));
+    }
+    double* dev = static_cast<double*>(c->stage.get(sizeof(double) * size_t(off[n_inst])));
     std::vector<const double*> ptrs(n_inst);
     for (int i = 0; i < n_inst; ++i) {
-      if (!sites_host[i]) fail(TN_ERR_INVALID, "NULL site buffer");
-      ck(cudaMemcpyAsync(dev + per * i, sites_host[i], sizeof(double) * per,
+      ck(cudaMemcpyAsync(dev + off[i], sites_host[i], sizeof(double) * plans[i]->site_elems,
                          cudaMemcpyHostToDevice, st),
          "copy sites");
-      ptrs[i] = dev + per * i;
+      ptrs[i] = dev + off[i];
     }
     tn_status r = tn_contract_approx(c, plans, n_inst, ptrs.data(), precision, learned_chi, stream);
     if (r != TN_OK) fail(r, c->err);
@@ -1362,6 +1539,192 @@ extern "C" tn_status tn_embed_tree_noalloc(int32_t n_inst, int32_t n_legs, const
        "copy status");
     for (int k = 0; k < n - 1; ++k) ranks_host[k] = st.r[k];
   });
+}
+
+extern "C" tn_status tn_autotune(tn_ctx_t* c, const tn_plan_t* const* plans, int32_t n_inst,
+                                 const double* const* sites_dev, int32_t precision,
+                                 const char* cache_path) {
+  if (!c) {
+    tn::set_error("tn_autotune: ctx is NULL");
+    return TN_ERR_INVALID;
+  }
+  return guarded(c, "tn_autotune", [&] {
+    if (!plans || !sites_dev || n_inst < 1) fail(TN_ERR_INVALID, "plans/sites NULL or n_inst < 1");
+    for (int i = 0; i < n_inst; ++i)
+      if (!plans[i] || !sites_dev[i]) fail(TN_ERR_INVALID, "NULL plan or site buffer");
+    if (precision == TN_PREC_FP64) return;  // no tensor-core contraction to tune
+    if (precision != TN_PREC_TF32 && precision != TN_PREC_TF32_FAST &&
+        precision != TN_PREC_TF32_GRAM)
+      fail(TN_ERR_UNSUPPORTED, "precision mode not implemented in this build");
+    if (!c->tc_ready) fail(TN_ERR_UNSUPPORTED, "tcgen05 path unavailable on this device");
+    ck(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaDeviceProp prop{};
+    ck(cudaGetDeviceProperties(&prop, c->device), "cudaGetDeviceProperties");
+    const std::string dev = prop.name;
+    // a cache written for this device replaces the table
+    if (cache_path) {
+      if (FILE* f = std::fopen(cache_path, "r")) {
+        std::map<std::array<int, 5>, std::array<int, 3>> t;
+        char line[512];
+        bool same_dev = false;
+        while (std::fgets(line, sizeof line, f)) {
+          if (std::strstr(line, "\"device\"") && std::strstr(line, dev.c_str())) same_dev = true;
+          int M, N, K, sp, bt, bn, kb, ns;
+          if (std::sscanf(line,
+                          " {\"M\": %d, \"N\": %d, \"K\": %d, \"split\": %d, \"batch\": %d, "
+                          "\"BN\": %d, \"budget_kb\": %d, \"ns\": %d}",
+                          &M, &N, &K, &sp, &bt, &bn, &kb, &ns) == 8)
+            t[{M, N, K, sp, bt}] = {bn, kb, ns};
+        }
+        std::fclose(f);
+        if (same_dev && !t.empty()) {
+          c->tune = std::move(t);
+          return;
+        }
+      }
+    }
+    cudaStream_t strm = nullptr;
+    c->tuning = true;
+    try {
+      run_batch(c, plans, n_inst, sites_dev, precision, false, strm, true);
+      ck(cudaStreamSynchronize(strm), "cudaStreamSynchronize");
+    } catch (...) {
+      c->tuning = false;
+      throw;
+    }
+    c->tuning = false;
+    c->pending = false;
+    if (cache_path) {
+      FILE* f = std::fopen(cache_path, "w");
+      if (!f) fail(TN_ERR_INVALID, std::string("cannot write ") + cache_path);
+      std::fprintf(f, "{\"format\": \"tn_dmtree tcgen05 tiles v1\",\n \"device\": \"%s\",\n \"entries\": [\n",
+                   dev.c_str());
+      size_t i = 0;
+      for (const auto& kv : c->tune) {
+        std::fprintf(f,
+                     "  {\"M\": %d, \"N\": %d, \"K\": %d, \"split\": %d, \"batch\": %d, \"BN\": %d, "
+                     "\"budget_kb\": %d, \"ns\": %d}%s\n",
+                     kv.first[0], kv.first[1], kv.first[2], kv.first[3], kv.first[4],
+                     kv.second[0], kv.second[1], kv.second[2], (++i < c->tune.size()) ? "," : "");
+      }
+      std::fprintf(f, " ]}\n");
+      std::fclose(f);
+    }
+  });
+}
+
+extern "C" tn_status tn_autotune_entries(const tn_ctx_t* c, int32_t* n_entries) {
+  if (!c || !n_entries) {
+    tn::set_error("tn_autotune_entries: NULL argument");
+    return TN_ERR_INVALID;
+  }
+  *n_entries = int32_t(c->tune.size());
+  return TN_OK;
+}
+
+// ---------------------------------------------------------------- graphs
+struct tn_batch_graph {
+  tn_ctx* own = nullptr;  // a private ctx: its workspace belongs to the graph
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int n = 0;
+};
+
+extern "C" tn_status tn_batch_graph_capture(tn_ctx_t* c, const tn_plan_t* const* plans, int32_t n_inst,
+                                      const double* const* sites_dev, int32_t precision,
+                                      tn_batch_graph_t** out) {
+  if (!c || !out) {
+    tn::set_error("tn_batch_graph_capture: ctx or out is NULL");
+    return TN_ERR_INVALID;
+  }
+  *out = nullptr;
+  tn_batch_graph* g = new (std::nothrow) tn_batch_graph();
+  if (!g) {
+    tn::set_error("tn_batch_graph_capture: host allocation failed");
+    return TN_ERR_OOM;
+  }
+  cudaStream_t cap = nullptr;
+  bool capturing = false;
+  tn_status s = guarded(c, "tn_batch_graph_capture", [&] {
+    if (!plans || !sites_dev || n_inst < 1) fail(TN_ERR_INVALID, "plans/sites NULL or n_inst < 1");
+    for (int i = 0; i < n_inst; ++i)
+      if (!plans[i] || !sites_dev[i]) fail(TN_ERR_INVALID, "NULL plan or site buffer");
+    if (precision != TN_PREC_FP64 && precision != TN_PREC_TF32 &&
+        precision != TN_PREC_TF32_FAST && precision != TN_PREC_TF32_GRAM)
+      fail(TN_ERR_UNSUPPORTED, "precision mode not implemented in this build");
+    const tn_status cs = tn_ctx_create(c->device, &g->own);
+    if (cs != TN_OK) fail(cs, tn::get_error());
+    if (precision != TN_PREC_FP64 && !g->own->tc_ready)
+      fail(TN_ERR_UNSUPPORTED, "tcgen05 path unavailable on this device");
+    g->own->eig_rounds = c->eig_rounds;
+    g->own->tune = c->tune;
+    g->n = n_inst;
+    ck(cudaDeviceSynchronize(), "cudaDeviceSynchronize");  // site buffers ready for cap
+    ck(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "cudaStreamCreate");
+    // one eager run sizes the workspace and places the tables
+    run_batch(g->own, plans, n_inst, sites_dev, precision, false, cap, true);
+    ck(cudaStreamSynchronize(cap), "cudaStreamSynchronize");
+    ck(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    capturing = true;
+    run_batch(g->own, plans, n_inst, sites_dev, precision, false, cap, false);
+    capturing = false;
+    ck(cudaStreamEndCapture(cap, &g->graph), "cudaStreamEndCapture");
+    ck(cudaGraphInstantiate(&g->exec, g->graph, 0), "cudaGraphInstantiate");
+    g->own->pending = false;
+  });
+  if (capturing && cap) {
+    cudaGraph_t junk = nullptr;
+    cudaStreamEndCapture(cap, &junk);
+    if (junk) cudaGraphDestroy(junk);
+    cudaGetLastError();
+  }
+  if (cap) cudaStreamDestroy(cap);
+  if (s != TN_OK) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->own) tn_ctx_destroy(g->own);
+    delete g;
+    return s;
+  }
+  *out = g;
+  return TN_OK;
+}
+
+extern "C" tn_status tn_batch_graph_launch(tn_batch_graph_t* g, void* stream) {
+  if (!g || !g->exec) {
+    tn::set_error("tn_batch_graph_launch: graph is NULL");
+    return TN_ERR_INVALID;
+  }
+  return guarded(g->own, "tn_batch_graph_launch", [&] {
+    ck(cudaSetDevice(g->own->device), "cudaSetDevice");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ck(cudaGraphLaunch(g->exec, st), "cudaGraphLaunch");
+    g->own->stream = st;
+    g->own->last_batch = g->n;
+    g->own->pending = true;
+  });
+}
+
+extern "C" tn_status tn_batch_graph_logz(tn_batch_graph_t* g, double* logz_host, int32_t* status_host,
+                                   int32_t n_inst) {
+  if (!g) {
+    tn::set_error("tn_batch_graph_logz: graph is NULL");
+    return TN_ERR_INVALID;
+  }
+  return tn_logz(g->own, logz_host, status_host, n_inst);
+}
+
+extern "C" tn_status tn_batch_graph_destroy(tn_batch_graph_t* g) {
+  if (!g) return TN_OK;
+  if (g->own) {
+    cudaSetDevice(g->own->device);
+    cudaDeviceSynchronize();
+  }
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  if (g->own) tn_ctx_destroy(g->own);
+  delete g;
+  return TN_OK;
 }
 
 extern "C" tn_status tn_ctx_set_option(tn_ctx_t* c, int32_t option, int64_t value) {

@@ -50,11 +50,13 @@ struct TcGemmArgs {
   int ct_cols;   // C^T store groups columns n = q * ct_cols + c into Ct[c][m * (N / ct_cols) + q]
   int* err;
   const int* poll;  // if set: a bounded wait on *poll != 0 first (expiry -> *err = 1)
+  int bn;           // tile width (multiple of 16, <= 256), 0: round_up(N, 16) capped at 256
+  int budget_kb;    // shared-memory budget of the K-chunk ring, 0: 104 KB (two CTAs per SM)
 };
 cudaError_t tc_gemm_configure();
 cudaError_t launch_sgemm_nt(const TcGemmArgs& g, cudaStream_t st);
 cudaError_t launch_tc_gemm(const TcGemmArgs& g, cudaStream_t st);
-size_t tc_gemm_smem_bytes(int BN, int split, int K, int* stages_out);
+size_t tc_gemm_smem_bytes(int BN, int split, int K, int* stages_out, int budget_kb = 104);
 
 cudaError_t launch_site_norm(const double* const* tens, const int64_t* off, const int64_t* len,
                              int nv, int batch, double* inv_norm, double* logscale, int* status,

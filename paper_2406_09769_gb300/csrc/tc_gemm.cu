@@ -397,15 +397,15 @@ bool make_map(CUtensorMap* m, const float* ptr, int K, int rows, int batch, long
 
 }  // namespace
 
-size_t tc_gemm_smem_bytes(int BN, int split, int K, int* stages_out) {
+size_t tc_gemm_smem_bytes(int BN, int split, int K, int* stages_out, int budget_kb) {
   // A ring of K-chunk stages (TMA targets), up to 4 and no more than the K
   // chunks, plus kLoBufs buffers for the lo halves of split chunks, within
-  // ~104 KB so that two CTAs share an SM (measured best for the per-instance
-  // 128 x 128 x 128..256 contractions: one CTA's loads and epilogue overlap
-  // the other's MMAs).
+  // the budget (default ~104 KB, so that two CTAs share an SM: one CTA's
+  // loads and epilogue overlap the other's MMAs; the autotuner also tries
+  // other budgets and tile widths per contraction shape).
   const size_t tile = size_t(128 + BN) * 128;
   const size_t lo = split ? kLoBufs * tile : 0;
-  const size_t budget = 104 * 1024;
+  const size_t budget = size_t(budget_kb > 0 ? budget_kb : 104) * 1024;
   int stages = budget > lo ? int((budget - lo) / tile) : 1;
   const int nk = (K + kChunk - 1) / kChunk;
   if (stages > nk) stages = nk;
@@ -435,11 +435,15 @@ cudaError_t launch_tc_gemm(const TcGemmArgs& g, cudaStream_t st) {
     return cudaErrorInvalidValue;
   int BN = ((g.N + 15) / 16) * 16;
   if (BN > 256) BN = 256;
+  if (g.bn > 0) {
+    if (g.bn % 16 || g.bn > 256) return cudaErrorInvalidValue;
+    BN = g.bn;
+  }
   CUtensorMap ma, mb;
   if (!make_map(&ma, g.A, g.K, g.M, g.batch, g.lda, g.sA, 128)) return cudaErrorInvalidValue;
   if (!make_map(&mb, g.B, g.K, g.N, g.batch, g.ldb, g.sB, BN)) return cudaErrorInvalidValue;
   int stages = 1;
-  const size_t smem = tc_gemm_smem_bytes(BN, g.split, g.K, &stages);
+  const size_t smem = tc_gemm_smem_bytes(BN, g.split, g.K, &stages, g.budget_kb);
   uint32_t cols = 32;
   while (cols < uint32_t(BN)) cols <<= 1;
   dim3 grid((g.N + BN - 1) / BN, (g.M + 127) / 128, g.batch);
