@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64-arm", action="store_true",
                    help="skip the FP64-path measurement beside the headline (N=1 only)")
+    p.add_argument("--no-batched-arm", action="store_true",
+                   help="skip the heterogeneous-batch measurement (N=1 only)")
     return p.parse_args()
 
 
@@ -150,6 +152,87 @@ def make_instances(first, count, size):
     from workloads import ising
     return [ising.lattice2d(size, size, 0.5, "gauss", seed=2 * 10**6 + first + i)
             for i in range(count)]
+
+
+HETERO_SIZES = (12, 16, 20, 24, 28, 32)
+HETERO_CHIS = (16, 32, 48, 64)
+
+
+def hetero_workload(n=256):
+    """Heterogeneous batch: instance i is an L x L open 2D Gaussian spin glass
+    (beta = 0.5) with L and chi drawn from the seeded generator (seed 4 * 10^6):
+    L uniform over HETERO_SIZES, chi uniform over HETERO_CHIS."""
+    from workloads import ising, prng
+    li = prng.randint(4 * 10**6, n, 0, len(HETERO_SIZES) - 1)
+    ci = prng.randint(4 * 10**6, n, 0, len(HETERO_CHIS) - 1, offset=n)
+    return [(HETERO_SIZES[li[i]], HETERO_CHIS[ci[i]],
+             ising.lattice2d(HETERO_SIZES[li[i]], HETERO_SIZES[li[i]], 0.5, "gauss",
+                             seed=4 * 10**6 + i)) for i in range(n)]
+
+
+def batched_arm(B, torch, local, stream, flush):
+    """The heterogeneous batch through one tn_contract_approx (untuned and
+    after tn_autotune) and through a captured CUDA graph, each timed over two
+    steps after one warm-up; parity: graph == eager bit for bit, and the
+    first twelve instances small enough for the oracle (L <= 16, chi <= 32)
+    against it."""
+    from oracle import dmtree
+    work = hetero_workload()
+    cache = {}
+    plans, bufs = [], []
+    for L, chi, w in work:
+        if (L, chi) not in cache:
+            cache[(L, chi)] = B.tn_plan(w["n"], w["edges"], np.full(len(w["edges"]), 2), chi,
+                                        env_size=L)
+        plans.append(cache[(L, chi)])
+        bufs.append(torch.from_numpy(B.pack_sites(plans[-1], w["tensors"])).to(local))
+    ptrs = [b.data_ptr() for b in bufs]
+    sh = stream.cuda_stream
+    ctx = B.tn_ctx_create(local.index if local.index is not None else 0)
+
+    def timed(fn, steps=2):
+        fn()
+        out = None
+        ms = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+        return len(plans) * steps / (ms / 1e3), ms / steps
+
+    eager = lambda: B.tn_contract_approx(ctx, plans, ptrs, B.TN_PREC_TF32, 0, sh)
+    v_untuned, ms_untuned = timed(eager)
+    lz_e0, st_e0 = B.tn_logz(ctx, len(plans))
+    t0 = time.perf_counter()
+    n_tuned = B.tn_autotune(ctx, plans, ptrs, B.TN_PREC_TF32)
+    tune_s = time.perf_counter() - t0
+    v_eager, ms_eager = timed(eager)
+    lz_e, st_e = B.tn_logz(ctx, len(plans))
+    g = B.Graph(ctx, plans, ptrs, B.TN_PREC_TF32)
+    v_graph, ms_graph = timed(lambda: g.launch(sh))
+    lz_g, st_g = g.logz()
+    small = [i for i, (L, chi, _) in enumerate(work) if L <= 16 and chi <= 32][:12]
+    errs = [abs(lz_g[i] - dmtree.partitioned_contract_rows(work[i][2], work[i][1])["logz"]) /
+            abs(lz_g[i]) for i in small]
+    return {"workload": "256 open 2D Gaussian spin glasses, beta 0.5, L in {12..32}, "
+                        "chi in {16, 32, 48, 64} per instance (seeded); stands in for the "
+                        "random 3-regular graphs, which need the general planner",
+            "buckets": len(cache), "instances": len(plans),
+            "untuned": {"value": v_untuned, "ms_per_step": ms_untuned},
+            "autotuned": {"value": v_eager, "ms_per_step": ms_eager, "shapes": n_tuned,
+                          "tuning_s": tune_s},
+            "graph_replay": {"value": v_graph, "ms_per_step": ms_graph},
+            "unit": "contractions/s",
+            "status_ok": int((st_g == 0).sum()),
+            "graph_equals_eager": bool(np.array_equal(lz_g, lz_e)),
+            "tuned_equals_untuned": bool(np.array_equal(lz_e, lz_e0)),
+            "oracle_instances": len(small),
+            "max_rel_logz_err_vs_oracle": float(max(errs)) if errs else None}
 
 
 def pack_all(B, plan, ws):
@@ -428,6 +511,10 @@ def bench_ours(args):
                     "steps": 1, "warmup": 1, "status_ok": int((st64 == 0).sum()),
                     "max_rel_logz_diff_vs_mixed": float(np.max(np.abs(lz64 - logz) / np.abs(lz64)))}
 
+    hetero = None
+    if world == 1 and not args.no_batched_arm:
+        hetero = batched_arm(B, torch, dev, stream, flush)
+
     out = {
         "metric": "approx contractions/s", "value": value, "unit": "contractions/s",
         "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": total_ms / K,
@@ -442,7 +529,7 @@ def bench_ours(args):
         "density_matrix_contractions": dm_group, "clocks": clocks,
         "status_ok": int((status == 0).sum()),
         "measured_peaks_tflops": {k: round(v, 2) for k, v in mp.items()},
-        "latency_batch1": lat, "fp64_arm": fp64_arm,
+        "latency_batch1": lat, "fp64_arm": fp64_arm, "batched_heterogeneous": hetero,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         d = run_oracle(0, args.size, args.chi, args.cpu_seconds)

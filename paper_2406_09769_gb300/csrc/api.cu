@@ -116,6 +116,10 @@ struct tn_ctx {
   // autotuned tensor-core tiles: {M, N, K, split, batch} -> {tile width, smem budget KB}
   std::map<std::array<int, 5>, std::array<int, 3>> tune;  // value: BN, budget KB, time (ns)
   bool tuning = false;
+  // concurrent buckets: a pool of streams with fork / join events
+  std::vector<cudaStream_t> pool;
+  std::vector<cudaEvent_t> joins;
+  cudaEvent_t fork = nullptr;
 };
 
 namespace {
@@ -160,7 +164,8 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // bytes: if set, receives the workspace size; with dry = true nothing is
 // allocated and the returned pointers are not valid.
-Ws carve(tn_ctx* c, const Dims& d, int B, int nv, bool dry = false, size_t* bytes = nullptr) {
+Ws carve(tn_ctx* c, const Dims& d, int B, int nv, bool dry = false, size_t* bytes = nullptr,
+         char* at = nullptr) {
   Ws w{};
   w.sS = d.maxS; w.sY = d.maxY; w.sR = d.maxR; w.sX = d.maxX; w.sM = d.maxM;
   w.sL = d.maxL; w.sP = d.maxP; w.sLam = d.maxLam; w.sAmax = d.maxN; w.sInv = nv;
@@ -176,7 +181,7 @@ Ws carve(tn_ctx* c, const Dims& d, int B, int nv, bool dry = false, size_t* byte
   tot += align256(sizeof(unsigned long long) * size_t(w.sAmax) * B);
   if (bytes) *bytes = tot;
   if (dry) return w;
-  char* base = static_cast<char*>(c->arena.get(tot));
+  char* base = at ? at : static_cast<char*>(c->arena.get(tot));
   double** outs[] = {&w.S0, &w.S1, &w.Y, &w.R, &w.X, &w.M, &w.G, &w.L, &w.P, &w.lam, &w.inv};
   for (int i = 0; i < 11; ++i) *outs[i] = reinterpret_cast<double*>(base + off[i]);
   w.amax = reinterpret_cast<unsigned long long*>(base + off[11]);
@@ -365,7 +370,8 @@ struct Bucket {
   std::vector<int> idx;                // instances of the batch, in order
   std::vector<const double*> sites;    // their site buffers
   std::vector<Lay> lay;
-  size_t ws_bytes = 0, tab_off = 0, res_off = 0;
+  size_t ws_bytes = 0, tab_off = 0, res_off = 0, ws_off = 0;
+  char* ws_at = nullptr;  // workspace slice (concurrent buckets), NULL: the arena
   std::vector<StepTables> tabs;
   const double** tens_table = nullptr;
   int64_t *off_dev = nullptr, *len_dev = nullptr;
@@ -527,7 +533,7 @@ void run_plan(tn_ctx* c, const Bucket& bk, int precision, bool learned, cudaStre
   const int B = int(bk.idx.size());
   const Dims dm = plan_dims(P);
   LearnState ls = learn_begin(c, P, B, learned, strm);
-  const Ws w = carve(c, dm, B, P->n_vertices);
+  const Ws w = carve(c, dm, B, P->n_vertices, false, nullptr, bk.ws_at);
   const double** tens_table = bk.tens_table;
   const int64_t* off_dev = bk.off_dev;
   const int64_t* len_dev = bk.len_dev;
@@ -587,7 +593,7 @@ struct WsF {
 };
 
 WsF carve_f32(tn_ctx* c, const tn_plan_t* P, const std::vector<Lay>& lay, int B,
-              bool dry = false, size_t* bytes = nullptr) {
+              bool dry = false, size_t* bytes = nullptr, char* at = nullptr) {
   long long maxS = 4, maxY = 4, maxR = 4, maxX = 4, maxM = 4, maxL = 4, maxP = 4, maxUt = 4,
             maxLam = 1;
   int maxN = 1;
@@ -629,7 +635,7 @@ WsF carve_f32(tn_ctx* c, const tn_plan_t* P, const std::vector<Lay>& lay, int B,
   tot += align256(sizeof(unsigned int) * size_t(w.sAmax) * B);
   if (bytes) *bytes = tot;
   if (dry) return w;
-  char* base = static_cast<char*>(c->arena.get(tot));
+  char* base = at ? at : static_cast<char*>(c->arena.get(tot));
   for (int i = 0; i < 12; ++i) *fout[i] = reinterpret_cast<float*>(base + off[i]);
   w.lam = reinterpret_cast<double*>(base + off[12]);
   w.inv = reinterpret_cast<double*>(base + off[13]);
@@ -790,7 +796,7 @@ void run_plan_tc(tn_ctx* c, const Bucket& bk, int sub_split, bool factored, bool
   const tn_plan_t* P = bk.P;
   const int B = int(bk.idx.size());
   const std::vector<Lay>& lay = bk.lay;
-  const WsF w = carve_f32(c, P, lay, B);
+  const WsF w = carve_f32(c, P, lay, B, false, nullptr, bk.ws_at);
   LearnState ls = learn_begin(c, P, B, learned, strm);
   const double** tens_table = bk.tens_table;
   const int64_t* off_dev = bk.off_dev;
@@ -849,6 +855,8 @@ void run_plan_tc(tn_ctx* c, const Bucket& bk, int sub_split, bool factored, bool
   }
 }
 
+constexpr size_t kPoolStreams = 8;  // concurrent buckets of one batch
+
 // Restores the ctx's result pointers after a bucketed batch (also on error).
 struct ResultView {
   tn_ctx* c;
@@ -904,7 +912,7 @@ void run_batch(tn_ctx* c, const tn_plan_t* const* plans, int n, const double* co
             fail(TN_ERR_UNSUPPORTED,
                  "TN_PREC_TF32 needs dim A_v <= 128, tree-edge dims <= 128 and ranks <= 64");
       }
-  size_t ws_max = 0, tab_tot = 0, res = 0;
+  size_t ws_max = 0, ws_sum = 0, tab_tot = 0, res = 0;
   std::vector<int> slot(n, 0);
   for (Bucket& bk : bks) {
     const int B = int(bk.idx.size());
@@ -914,6 +922,8 @@ void run_batch(tn_ctx* c, const tn_plan_t* const* plans, int n, const double* co
     else
       carve(c, plan_dims(bk.P), B, bk.P->n_vertices, true, &bk.ws_bytes);
     ws_max = std::max(ws_max, bk.ws_bytes);
+    bk.ws_off = ws_sum;
+    ws_sum += align256(bk.ws_bytes);
     bk.tab_off = tab_tot;
     tab_tot += align256(tables_bytes(bk.P, B));
     bk.res_off = res;
@@ -921,7 +931,24 @@ void run_batch(tn_ctx* c, const tn_plan_t* const* plans, int n, const double* co
     res += B;
   }
   ensure_results(c, n);
-  c->arena.get(ws_max);
+  // several buckets run concurrently on a pool of streams, each in a
+  // workspace slice of its own (the learned ranks keep one bucket)
+  const int nstreams = bks.size() > 1 ? int(std::min<size_t>(bks.size(), kPoolStreams)) : 0;
+  if (nstreams) {
+    char* wbase = static_cast<char*>(c->arena.get(ws_sum));
+    for (Bucket& bk : bks) bk.ws_at = wbase + bk.ws_off;
+    while (int(c->pool.size()) < nstreams) {
+      cudaStream_t ps = nullptr;
+      ck(cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking), "cudaStreamCreate");
+      c->pool.push_back(ps);
+      cudaEvent_t ev = nullptr;
+      ck(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "cudaEventCreate");
+      c->joins.push_back(ev);
+    }
+    if (!c->fork) ck(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming), "cudaEventCreate");
+  } else {
+    c->arena.get(ws_max);
+  }
   char* dbase = static_cast<char*>(c->tables.get(tab_tot));
   char* h = upload ? static_cast<char*>(pinned_get(c, tab_tot)) : nullptr;
   for (Bucket& bk : bks)
@@ -935,13 +962,30 @@ void run_batch(tn_ctx* c, const tn_plan_t* const* plans, int n, const double* co
   ck(cudaMemsetAsync(c->err_flag, 0, 2 * sizeof(int), strm), "memset err");
   {
     ResultView view(c);
-    for (const Bucket& bk : bks) {
+    if (nstreams) {
+      ck(cudaEventRecord(c->fork, strm), "cudaEventRecord");
+      for (int q = 0; q < nstreams; ++q)
+        ck(cudaStreamWaitEvent(c->pool[q], c->fork, 0), "cudaStreamWaitEvent");
+    }
+    // largest buckets first, dealt round-robin over the streams
+    std::vector<size_t> order(bks.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t a, size_t b) { return bks[a].ws_bytes > bks[b].ws_bytes; });
+    for (size_t j = 0; j < order.size(); ++j) {
+      const Bucket& bk = bks[order[j]];
+      cudaStream_t bs = nstreams ? c->pool[j % nstreams] : strm;
       view.at(bk.res_off);
       if (tc)
-        run_plan_tc(c, bk, sub_split, factored, learned, strm);
+        run_plan_tc(c, bk, sub_split, factored, learned, bs);
       else
-        run_plan(c, bk, precision, learned, strm);
+        run_plan(c, bk, precision, learned, bs);
     }
+    if (nstreams)
+      for (int q = 0; q < nstreams; ++q) {
+        ck(cudaEventRecord(c->joins[q], c->pool[q]), "cudaEventRecord");
+        ck(cudaStreamWaitEvent(strm, c->joins[q], 0), "cudaStreamWaitEvent");
+      }
   }
   c->slot = std::move(slot);
   c->slot_identity = bks.size() == 1;
@@ -1024,6 +1068,9 @@ extern "C" tn_status tn_ctx_destroy(tn_ctx_t* c) {
   c->aux_buf.release();
   if (c->pinned) cudaFreeHost(c->pinned);
   if (c->pinned_free) cudaEventDestroy(c->pinned_free);
+  for (cudaStream_t ps : c->pool) cudaStreamDestroy(ps);
+  for (cudaEvent_t ev : c->joins) cudaEventDestroy(ev);
+  if (c->fork) cudaEventDestroy(c->fork);
   delete c;
   return TN_OK;
 }
