@@ -187,7 +187,13 @@ tn_status tn_embed_tree(tn_ctx_t* ctx, int32_t n_inst, int32_t n_legs,
  * Asynchronous on stream; results are read with tn_logz.  learned_chi = 0
  * keeps each edge's plan rank r_k; learned_chi = 1 lets the rank model of
  * ctx (tn_rank_model_load; TN_ERR_INVALID if none is loaded) choose a rank
- * chi_k <= r_k per edge under a per-pass budget (see "learned ranks").     */
+ * chi_k <= r_k per edge under a per-pass budget (see "learned ranks");
+ * learned_chi = 2 runs the batch twice, at the uniform ranks
+ * min(chi_uniform, r_k) and with the learned ranks, and keeps per instance
+ * the ln Z of the run whose summed discarded share sum_k sum_{j >= chi_k}
+ * lam_j / sum_j lam_j is smaller (the uniform method judges the model;
+ * tn_rank_judged tells which run each instance kept).  Learned ranks need
+ * all instances of the batch to share one plan structure.                  */
 tn_status tn_contract_approx(tn_ctx_t* ctx, const tn_plan_t* const* plans, int32_t n_inst,
                              const double* const* sites_dev, int32_t precision,
                              int32_t learned_chi, void* stream);
@@ -319,6 +325,10 @@ tn_status tn_rank_model_load(tn_ctx_t* ctx, const float* weights_host, int32_t n
  * unless learned_chi = 1.  The buffers must stay valid until tn_logz.      */
 tn_status tn_rank_record(tn_ctx_t* ctx, float* feat_dev, double* spec_dev, int32_t* chi_dev,
                          double* acc_dev, int64_t cap_edges);
+
+/* After a tn_contract_approx with learned_chi = 2 (synchronous): used[i] = 1
+ * where instance i kept the learned-rank run, 0 where the uniform run.      */
+tn_status tn_rank_judged(tn_ctx_t* ctx, int32_t* used_learned_host, int32_t n_inst);
 
 /* Training labels: for every pass p (edges pass_start[p] .. pass_start[p+1]-1,
  * at most 256 per pass; host array of n_pass + 1 entries, n_pass <= 65535)

@@ -59,7 +59,7 @@ EXPORTS = ("tn_plan", "tn_plan_destroy", "tn_plan_query", "tn_plan_site_offset",
            "tn_ctx_create", "tn_ctx_destroy", "tn_embed_tree", "tn_contract_approx",
            "tn_logz", "tn_contract_approx_host", "tn_embed_tree_noalloc",
            "tn_rank_model_params", "tn_rank_model_load", "tn_rank_record", "tn_rank_labels",
-           "tn_rank_model_grad", "tn_rank_model_train",
+           "tn_rank_model_grad", "tn_rank_model_train", "tn_rank_judged",
            "tn_ctx_set_option", "tn_ctx_set_profiling", "tn_ctx_profile", "tn_measure_peaks",
            "tn_autotune", "tn_autotune_entries", "tn_batch_graph_capture", "tn_batch_graph_launch",
            "tn_batch_graph_logz", "tn_batch_graph_destroy", "tn_last_error")
@@ -105,6 +105,7 @@ def lib():
     L.tn_rank_model_train.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.c_float, _vp, _vp, _vp]
     L.tn_ctx_set_option.argtypes = [_vp, ctypes.c_int32, ctypes.c_int64]
+    L.tn_rank_judged.argtypes = [_vp, _i32p, ctypes.c_int32]
     L.tn_autotune.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.c_int32, ctypes.POINTER(_vp),
                               ctypes.c_int32, ctypes.c_char_p]
     L.tn_autotune_entries.argtypes = [_vp, _i32p]
@@ -358,6 +359,13 @@ def tn_ctx_profile(ctx):
 
 
 TN_OPT_EIG_ROUNDS, TN_OPT_WAIT_PROBE = 1, 2
+
+
+def tn_rank_judged(ctx, n_inst):
+    """Which run each instance of the last judged batch kept (1 = learned)."""
+    used = np.empty(n_inst, dtype=np.int32)
+    _check(lib().tn_rank_judged(ctx.handle, used.ctypes.data_as(_i32p), int(n_inst)), ctx)
+    return used
 
 
 def tn_autotune(ctx, plans, sites_dev, precision=TN_PREC_TF32, cache_path=None):

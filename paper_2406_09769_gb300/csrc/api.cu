@@ -101,6 +101,12 @@ struct tn_ctx {
   int64_t rec_cap = 0;     // edges (eigensolves) the record buffers hold per instance
   DevBuf train_buf;        // gradient and Adam moments
   DevBuf aux_buf;          // label tables, sample indices
+  // the uniform-chi judge of learned ranks (learned_chi = 2)
+  int hook_fixed_chi = 0;  // > 0: the rank hook keeps min(chi_uniform, r_v), no model
+  double* hook_acc = nullptr;  // overrides rec_acc as the discarded-share accumulator
+  DevBuf judge_buf;        // acc_l, acc_u, logz_u, status_u, used
+  int* judged = nullptr;   // per instance: 1 = learned run kept (last judged batch)
+  int judged_n = 0;
   // device pointers carved from `results`
   double* logz = nullptr;
   int* status = nullptr;
@@ -416,13 +422,13 @@ struct LearnState {
 
 LearnState learn_begin(tn_ctx* c, const tn_plan_t* P, int B, bool learned, cudaStream_t strm) {
   LearnState s;
-  s.learned = learned;
-  s.record = c->rec_feat || c->rec_spec || c->rec_chi || c->rec_acc;
+  s.learned = learned || c->hook_fixed_chi > 0;
+  s.record = c->hook_fixed_chi == 0 && (c->rec_feat || c->rec_spec || c->rec_chi || c->rec_acc);
   s.npass = std::max(1, int(P->info.n_dm_passes));
   if (s.learned || s.record) {
     s.budget_rem = static_cast<int*>(c->learn_buf.get(2 * sizeof(int) * size_t(B)));
-    if (c->rec_acc)
-      ck(cudaMemsetAsync(c->rec_acc, 0, sizeof(double) * size_t(B), strm), "memset acc");
+    double* acc = c->hook_acc ? c->hook_acc : c->rec_acc;
+    if (acc) ck(cudaMemsetAsync(acc, 0, sizeof(double) * size_t(B), strm), "memset acc");
   }
   return s;
 }
@@ -449,7 +455,8 @@ void rank_hook(tn_ctx* c, const PassCtx* pc, const tn::Step& st, int k, int A, i
   tn::RankArgs g{};
   g.lam = lam; g.slam = slam; g.A = A; g.rk = rk; g.dk = st.d[k];
   g.v = k; g.nlegs = st.n; g.pass = pc->pass; g.npass = pc->npass;
-  g.model = pc->learned ? c->model_buf.p : nullptr;
+  g.model = (pc->learned && c->hook_fixed_chi == 0) ? c->model_buf.p : nullptr;
+  g.fixed_chi = c->hook_fixed_chi;
   g.budget_total = pc->budget_total;
   g.chi_uniform = c->chi_uniform;
   g.edges_after = st.n - 2 - k;
@@ -458,7 +465,7 @@ void rank_hook(tn_ctx* c, const PassCtx* pc, const tn::Step& st, int k, int A, i
   g.first = (k == 1);
   g.budget_rem = pc->budget_rem;
   g.prev_chi = pc->budget_rem + B;
-  g.acc = c->rec_acc;
+  g.acc = c->hook_acc ? c->hook_acc : c->rec_acc;
   const long long e = pc->edge ? (*pc->edge)++ : 0;
   if (pc->record && e < c->rec_cap) {
     g.rec_chi = c->rec_chi; g.rec_feat = c->rec_feat; g.rec_spec = c->rec_spec;
@@ -1066,6 +1073,7 @@ extern "C" tn_status tn_ctx_destroy(tn_ctx_t* c) {
   c->learn_buf.release();
   c->train_buf.release();
   c->aux_buf.release();
+  c->judge_buf.release();
   if (c->pinned) cudaFreeHost(c->pinned);
   if (c->pinned_free) cudaEventDestroy(c->pinned_free);
   for (cudaStream_t ps : c->pool) cudaStreamDestroy(ps);
@@ -1085,7 +1093,12 @@ extern "C" tn_status tn_contract_approx(tn_ctx_t* c, const tn_plan_t* const* pla
   return guarded(c, "tn_contract_approx", [&] {
     if (!plans || !sites_dev || n_inst < 1) fail(TN_ERR_INVALID, "plans/sites NULL or n_inst < 1");
     if (learned_chi && !c->have_model)
-      fail(TN_ERR_INVALID, "learned_chi = 1 needs a rank model (tn_rank_model_load)");
+      fail(TN_ERR_INVALID, "learned_chi = 1 or 2 needs a rank model (tn_rank_model_load)");
+    if (learned_chi < 0 || learned_chi > 2) fail(TN_ERR_INVALID, "learned_chi must be 0, 1 or 2");
+    if (learned_chi)
+      for (int i = 1; i < n_inst; ++i)
+        if (plans[i] && !tn::plans_equivalent(plans[0], plans[i]))
+          fail(TN_ERR_UNSUPPORTED, "learned ranks need one plan structure per batch");
     for (int i = 0; i < n_inst; ++i)
       if (!plans[i] || !sites_dev[i]) fail(TN_ERR_INVALID, "NULL plan or site buffer");
     ck(cudaSetDevice(c->device), "cudaSetDevice");
@@ -1096,7 +1109,59 @@ extern "C" tn_status tn_contract_approx(tn_ctx_t* c, const tn_plan_t* const* pla
     } else if (precision != TN_PREC_FP64) {
       fail(TN_ERR_UNSUPPORTED, "precision mode not implemented in this build");
     }
-    run_batch(c, plans, n_inst, sites_dev, precision, learned_chi != 0, strm, true);
+    if (learned_chi == 2) {
+      // the uniform-chi judge: a run at min(chi_uniform, r_v), then the
+      // learned run; per instance the smaller summed discarded share wins
+      const size_t nb = size_t(n_inst);
+      char* jb = static_cast<char*>(c->judge_buf.get(4 * align256(sizeof(double) * nb) +
+                                                      2 * align256(sizeof(int) * nb)));
+      double* acc_l = reinterpret_cast<double*>(jb);
+      double* acc_u = reinterpret_cast<double*>(jb + align256(sizeof(double) * nb));
+      double* logz_u = reinterpret_cast<double*>(jb + 2 * align256(sizeof(double) * nb));
+      int* status_u = reinterpret_cast<int*>(jb + 3 * align256(sizeof(double) * nb));
+      int* used = status_u + align256(sizeof(int) * nb) / sizeof(int);
+      struct Reset {
+        tn_ctx* c;
+        ~Reset() {
+          c->hook_fixed_chi = 0;
+          c->hook_acc = nullptr;
+        }
+      } reset{c};
+      c->hook_fixed_chi = c->chi_uniform;
+      c->hook_acc = acc_u;
+      run_batch(c, plans, n_inst, sites_dev, precision, false, strm, true);
+      ck(cudaMemcpyAsync(logz_u, c->logz, sizeof(double) * nb, cudaMemcpyDeviceToDevice, strm),
+         "copy logz");
+      ck(cudaMemcpyAsync(status_u, c->status, sizeof(int) * nb, cudaMemcpyDeviceToDevice, strm),
+         "copy status");
+      c->hook_fixed_chi = 0;
+      c->hook_acc = c->rec_acc ? nullptr : acc_l;
+      run_batch(c, plans, n_inst, sites_dev, precision, true, strm, true);
+      ck(tn::launch_judge_select(c->rec_acc ? c->rec_acc : acc_l, acc_u, logz_u, status_u,
+                                 c->logz, c->status, used, n_inst, strm),
+         "judge");
+      c->judged = used;
+      c->judged_n = n_inst;
+    } else {
+      run_batch(c, plans, n_inst, sites_dev, precision, learned_chi != 0, strm, true);
+      c->judged = nullptr;
+    }
+  });
+}
+
+extern "C" tn_status tn_rank_judged(tn_ctx_t* c, int32_t* used_learned_host, int32_t n_inst) {
+  if (!c) {
+    tn::set_error("tn_rank_judged: ctx is NULL");
+    return TN_ERR_INVALID;
+  }
+  return guarded(c, "tn_rank_judged", [&] {
+    if (!used_learned_host || !c->judged || n_inst != c->judged_n)
+      fail(TN_ERR_INVALID, "no judged batch of this size (learned_chi = 2) has run");
+    ck(cudaSetDevice(c->device), "cudaSetDevice");
+    ck(cudaMemcpyAsync(used_learned_host, c->judged, sizeof(int) * n_inst,
+                       cudaMemcpyDeviceToHost, c->stream),
+       "copy judged");
+    ck(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
   });
 }
 

@@ -118,6 +118,7 @@ struct RankArgs {
   int* prev_chi;                      // per-instance rank kept at the previous vertex
   double* acc;                        // per-instance summed discarded share (or NULL)
   int* rec_chi; float* rec_feat; double* rec_spec; long long rec_off;  // optional records
+  int fixed_chi;                      // no model: keep min(fixed_chi, r_v) (0: r_v)
 };
 int rank_model_params();
 template <typename T>
@@ -132,6 +133,12 @@ cudaError_t launch_water_fill(const double* spec, const int* cap, const int* pas
                               int chi_u, int n_pass, int B, int* chi_out, float* feat,
                               cudaStream_t st);
 int water_fill_max_edges();
+// Per instance: keep ln Z / status of the run with the smaller summed discarded
+// share (learned run: logz, status in place; uniform run: logz_u, status_u);
+// used[i] = 1 where the learned run is kept.
+cudaError_t launch_judge_select(const double* acc_l, const double* acc_u, const double* logz_u,
+                                const int* status_u, double* logz, int* status, int* used,
+                                int n, cudaStream_t st);
 cudaError_t launch_iota(int* x, int n, cudaStream_t st);
 
 // Factored density matrices (svd.cu).  launch_chol_env: every memoised

@@ -99,6 +99,7 @@ __global__ void __launch_bounds__(64) k_rank_select(RankArgs g, T* U, long long 
                   min(g.chi_uniform, g.rk), f);
   __syncthreads();
   int chi = rk;
+  if (!g.model && g.fixed_chi > 0) chi = min(rk, g.fixed_chi);  // uniform chi (the judge's run)
   if (g.model) {
     const __nv_bfloat16* W = static_cast<const __nv_bfloat16*>(g.model);
     float z = bfv(W, ob1 + t);
@@ -399,6 +400,29 @@ cudaError_t launch_water_fill(const double* spec, const int* cap, const int* pas
 }
 
 int water_fill_max_edges() { return 32 * kWfLane; }
+
+namespace {
+__global__ void k_judge_select(const double* acc_l, const double* acc_u, const double* logz_u,
+                               const int* status_u, double* logz, int* status, int* used, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const bool keep = acc_l[i] <= acc_u[i];
+  if (!keep) {
+    logz[i] = logz_u[i];
+    status[i] = status_u[i];
+  }
+  used[i] = keep ? 1 : 0;
+}
+}  // namespace
+
+cudaError_t launch_judge_select(const double* acc_l, const double* acc_u, const double* logz_u,
+                                const int* status_u, double* logz, int* status, int* used,
+                                int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_judge_select<<<(n + 127) / 128, 128, 0, st>>>(acc_l, acc_u, logz_u, status_u, logz, status,
+                                                  used, n);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_iota(int* x, int n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;

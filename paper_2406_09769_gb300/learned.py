@@ -123,18 +123,18 @@ def fit(ctx, plans_max, sites_dev, chi_uniform, precision=B.TN_PREC_FP64, steps=
 
 
 def contract(ctx, plans_max, sites_dev, weights, chi_uniform, precision=B.TN_PREC_FP64,
-             plans_uniform=None):
-    """ln Z with learned ranks.  With plans_uniform (the chi_uniform plans) the
-    uniform-chi method judges each instance: the result with the smaller summed
-    discarded share is returned.  Returns (logz, status, used_learned)."""
+             judged=True):
+    """ln Z with learned ranks; with judged (the default) the library also runs
+    the uniform chi_uniform ranks and keeps, per instance, the run with the
+    smaller summed discarded share (tn_contract_approx with learned_chi = 2).
+    Returns (logz, status, used_learned)."""
     B.tn_rank_model_load(ctx, weights, chi_uniform)
-    lr_ = record(ctx, plans_max, sites_dev, precision, learned=True)
-    logz, status = lr_.logz.copy(), lr_.status.copy()
-    used = np.ones(len(plans_max), dtype=bool)
-    if plans_uniform is not None:
-        ur = record(ctx, plans_uniform, sites_dev, precision)
-        acc_l, acc_u = lr_.acc.cpu().numpy(), ur.acc.cpu().numpy()
-        used = acc_l <= acc_u
-        logz = np.where(used, logz, ur.logz)
-        status = np.where(used, status, ur.status)
+    ptrs = [int(p) for p in sites_dev]
+    B.tn_contract_approx(ctx, plans_max, ptrs, precision, 2 if judged else 1,
+                         torch.cuda.current_stream().cuda_stream)
+    logz, status = B.tn_logz(ctx, len(plans_max))
+    if judged:
+        used = B.tn_rank_judged(ctx, len(plans_max)).astype(bool)
+    else:
+        used = np.ones(len(plans_max), dtype=bool)
     return logz, status, used
