@@ -1384,6 +1384,78 @@ extern "C" tn_status tn_contract_approx_host(tn_ctx_t* c, const tn_plan_t* const
   return tn_logz(c, logz_host, status_host, n_inst);
 }
 
+namespace {
+// One factored mixed-precision pass on explicit FP64 blocks (tn_embed_tree
+// with TN_PREC_TF32): blocks converted to the FP32 layout (with the
+// transposed copies the tensor-core contractions read), dm_pass_tc, and the
+// tree tensors converted back to the caller's packed FP64 layout.
+void embed_tree_tc(tn_ctx* c, const tn::Step& st, const tn_plan_t* tmp, int B,
+                   const double* const* blocks_dev, double* const* tree_dev, double* lognorm_dev,
+                   int32_t* status_dev, cudaStream_t strm) {
+  const int n = st.n;
+  const std::vector<Lay> lay{lay_f32(st)};
+  const Lay& l = lay[0];
+  ensure_results(c, B);
+  const WsF w = carve_f32(c, tmp, lay, B);
+  // tables: block pointers, tree pointers, conversion segments, R_k offsets and D
+  const size_t o_in = 0, o_out = align256(sizeof(void*) * B);
+  const size_t o_seg_in = o_out + align256(sizeof(void*) * B);
+  const size_t o_seg_out = o_seg_in + align256(sizeof(tn::CvtSeg) * n);
+  const size_t o_roff = o_seg_out + align256(sizeof(tn::CvtSeg) * n);
+  const size_t o_D = o_roff + align256(sizeof(int64_t) * n);
+  const size_t tot = o_D + align256(sizeof(int32_t) * (n + 1));
+  char* h = static_cast<char*>(pinned_get(c, tot));
+  char* d = static_cast<char*>(c->tables.get(tot));
+  std::memcpy(h + o_in, blocks_dev, sizeof(void*) * B);
+  std::memcpy(h + o_out, tree_dev, sizeof(void*) * B);
+  tn::CvtSeg* si = reinterpret_cast<tn::CvtSeg*>(h + o_seg_in);
+  tn::CvtSeg* so = reinterpret_cast<tn::CvtSeg*>(h + o_seg_out);
+  int max_in = 1, max_out = 1;
+  int64_t out_pos = 0;
+  for (int k = 0; k < n; ++k) {
+    const int rows = st.site[k].a, cols = st.d[k] * st.D[k];
+    si[k] = tn::CvtSeg{st.y_off[k], l.y_off[k], rows, cols};
+    max_in = std::max(max_in, rows * cols);
+  }
+  for (int k = 1; k < n; ++k) {  // tree tensors U_1 .. U_{n-2}, then the root
+    const int64_t sz = st.s_size[k];
+    so[k - 1] = tn::CvtSeg{l.s_off[k], out_pos, 1, int32_t(sz)};
+    out_pos += sz;
+    max_out = std::max<int>(max_out, int(sz));
+  }
+  std::vector<int64_t> ro(l.r_off);
+  ro.resize(n, 0);
+  std::memcpy(h + o_roff, ro.data(), sizeof(int64_t) * n);
+  std::vector<int32_t> Dv(st.D);
+  int mx = 1;
+  for (int x : Dv) mx = std::max(mx, x);
+  Dv.push_back(mx);
+  std::memcpy(h + o_D, Dv.data(), sizeof(int32_t) * (n + 1));
+  ck(cudaMemcpyAsync(d, h, tot, cudaMemcpyHostToDevice, strm), "upload tables");
+  ck(cudaEventRecord(c->pinned_free, strm), "cudaEventRecord");
+  ck(cudaMemsetAsync(c->logscale, 0, sizeof(double) * B, strm), "memset");
+  ck(cudaMemsetAsync(c->status, 0, sizeof(int) * B, strm), "memset");
+  ck(cudaMemsetAsync(c->err_flag, 0, 2 * sizeof(int), strm), "memset err");
+  ck(tn::launch_convert_segments_d2f(reinterpret_cast<const double* const*>(d + o_in), w.Y, w.sY,
+                                     w.Yt, reinterpret_cast<const tn::CvtSeg*>(d + o_seg_in), n,
+                                     max_in, B, strm),
+     "convert blocks");
+  StepTables tab{};
+  tab.r_off = reinterpret_cast<int64_t*>(d + o_roff);
+  tab.D = reinterpret_cast<int32_t*>(d + o_D);
+  dm_pass_tc(c, st, l, w, w.S1, B, 1, true, &tab, strm);
+  ck(tn::launch_convert_segments_f2d(w.S1, w.sS, reinterpret_cast<double* const*>(d + o_out),
+                                     reinterpret_cast<const tn::CvtSeg*>(d + o_seg_out), n - 1,
+                                     max_out, B, strm),
+     "convert tree");
+  ck(cudaMemcpyAsync(lognorm_dev, c->logscale, sizeof(double) * B, cudaMemcpyDeviceToDevice,
+                     strm),
+     "copy lognorm");
+  ck(cudaMemcpyAsync(status_dev, c->status, sizeof(int) * B, cudaMemcpyDeviceToDevice, strm),
+     "copy status");
+}
+}  // namespace
+
 extern "C" tn_status tn_embed_tree(tn_ctx_t* c, int32_t n_inst, int32_t n_legs,
                                    const int32_t* leg_dim, const int32_t* bond_dim,
                                    const double* const* blocks_dev, int32_t chi,
@@ -1399,8 +1471,10 @@ extern "C" tn_status tn_embed_tree(tn_ctx_t* c, int32_t n_inst, int32_t n_legs,
         !lognorm_dev || !status_dev || !ranks_host)
       fail(TN_ERR_INVALID, "invalid argument");
     if (chi < 1 && !chi_per_edge) fail(TN_ERR_INVALID, "chi must be >= 1");
-    if (precision != TN_PREC_FP64)
-      fail(TN_ERR_UNSUPPORTED, "this build runs the FP64 path only (precision 0)");
+    if (precision != TN_PREC_FP64 && precision != TN_PREC_TF32)
+      fail(TN_ERR_UNSUPPORTED, "tn_embed_tree runs TN_PREC_FP64 or TN_PREC_TF32");
+    if (precision == TN_PREC_TF32 && !c->tc_ready)
+      fail(TN_ERR_UNSUPPORTED, "tcgen05 path unavailable on this device");
     const int n = n_legs;
     tn::Step st;
     st.kind = 1;
@@ -1463,9 +1537,18 @@ extern "C" tn_status tn_embed_tree(tn_ctx_t* c, int32_t n_inst, int32_t n_legs,
     st.r_total = off;
     tn_plan_t tmp;
     tmp.steps.push_back(st);
-    const Dims dm = plan_dims(&tmp);
     ck(cudaSetDevice(c->device), "cudaSetDevice");
     cudaStream_t strm = static_cast<cudaStream_t>(stream);
+    if (precision == TN_PREC_TF32) {
+      for (int k = 1; k <= n - 2; ++k)
+        if (!tn::svd_left_supported(st.r[k - 1] * st.d[k], st.D[k], st.r[k]))
+          fail(TN_ERR_UNSUPPORTED,
+               "TN_PREC_TF32 needs dim A_v <= 128, tree-edge dims <= 128 and ranks <= 64");
+      embed_tree_tc(c, st, &tmp, n_inst, blocks_dev, tree_dev, lognorm_dev, status_dev, strm);
+      for (int k = 0; k < n - 1; ++k) ranks_host[k] = st.r[k];
+      return;
+    }
+    const Dims dm = plan_dims(&tmp);
     ensure_results(c, n_inst);
     const Ws w = carve(c, dm, n_inst, 1);
     ck(cudaMemsetAsync(c->logscale, 0, sizeof(double) * n_inst, strm), "memset");

@@ -103,6 +103,18 @@ cudaError_t launch_root_f32(const float* P, long long sP, int ldp, const float* 
 cudaError_t launch_close_f32(const float* Y, long long sY, const int64_t* y_off, const int32_t* D,
                              int n, int maxD, const double* logscale, double* logz, int* status,
                              int batch, cudaStream_t st);
+// Segment conversions between the caller's FP64 buffers and FP32 workspace
+// (one pass on explicit blocks in the mixed precision, tn_embed_tree).
+struct CvtSeg {
+  int64_t src_off, dst_off;
+  int32_t rows, cols;
+};
+cudaError_t launch_convert_segments_d2f(const double* const* src_tab, float* dst_base,
+                                        long long s_dst, float* dst_t, const CvtSeg* segs,
+                                        int nseg, int max_elems, int batch, cudaStream_t st);
+cudaError_t launch_convert_segments_f2d(const float* src_base, long long s_src,
+                                        double* const* dst_tab, const CvtSeg* segs, int nseg,
+                                        int max_elems, int batch, cudaStream_t st);
 // ---- learned per-edge rank allocation (learned.cu)
 constexpr int kRankFeatures = 22;
 constexpr int kRankHidden = 64;

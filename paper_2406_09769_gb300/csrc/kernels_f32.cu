@@ -488,4 +488,52 @@ cudaError_t launch_close_f32(const float* Y, long long sY, const int64_t* y_off,
   return cudaGetLastError();
 }
 
+namespace {
+// One segment per tree position: a rows x cols row-major matrix at src_off of
+// every instance's source buffer, converted to dst_off of its destination
+// buffer (and, with dst_t, its transpose at the same offset of dst_t).
+template <typename S, typename D>
+__global__ void __launch_bounds__(256) k_convert_segments(const S* const* src_tab,
+                                                          const S* src_base, long long s_src,
+                                                          D* const* dst_tab, D* dst_base,
+                                                          long long s_dst, D* dst_t,
+                                                          const CvtSeg* __restrict__ segs) {
+  const CvtSeg sg = segs[blockIdx.y];
+  const int i = blockIdx.z;
+  const S* src = (src_tab ? src_tab[i] : src_base + (long long)i * s_src) + sg.src_off;
+  D* dst = (dst_tab ? dst_tab[i] : dst_base + (long long)i * s_dst) + sg.dst_off;
+  D* dt = dst_t ? dst_t + (long long)i * s_dst + sg.dst_off : nullptr;
+  const long long total = (long long)sg.rows * sg.cols;
+  for (long long idx = blockIdx.x * 256ll + threadIdx.x; idx < total;
+       idx += 256ll * gridDim.x) {
+    const D x = D(src[idx]);
+    dst[idx] = x;
+    if (dt) {
+      const long long r = idx / sg.cols, c = idx - r * sg.cols;
+      dt[c * sg.rows + r] = x;
+    }
+  }
+}
+}  // namespace
+
+cudaError_t launch_convert_segments_d2f(const double* const* src_tab, float* dst_base,
+                                        long long s_dst, float* dst_t, const CvtSeg* segs,
+                                        int nseg, int max_elems, int batch, cudaStream_t st) {
+  if (nseg < 1 || batch < 1) return cudaSuccess;
+  dim3 grid((max_elems + 255) / 256, nseg, batch);
+  k_convert_segments<double, float><<<grid, 256, 0, st>>>(src_tab, nullptr, 0, nullptr, dst_base,
+                                                          s_dst, dst_t, segs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_segments_f2d(const float* src_base, long long s_src,
+                                        double* const* dst_tab, const CvtSeg* segs, int nseg,
+                                        int max_elems, int batch, cudaStream_t st) {
+  if (nseg < 1 || batch < 1) return cudaSuccess;
+  dim3 grid((max_elems + 255) / 256, nseg, batch);
+  k_convert_segments<float, double><<<grid, 256, 0, st>>>(nullptr, src_base, s_src, dst_tab,
+                                                          nullptr, 0, nullptr, segs);
+  return cudaGetLastError();
+}
+
 }  // namespace tn

@@ -17,14 +17,15 @@
 // The SVD follows the bisection-and-inverse-iteration route of Marques,
 // Demmel and Vasconcelos (LAPACK xBDSVDX):
 //   a. Golub-Kahan bidiagonalisation K = H B G^T by Householder reflectors
-//      (Golub & Van Loan, Matrix Computations, Sec. 5.4.8), K in shared
-//      memory, left reflectors kept, right reflectors dropped;
+//      (Golub & Van Loan, Matrix Computations, Sec. 5.4.8), K in register
+//      tiles, left reflectors kept, right reflectors dropped;
 //   b. the r largest eigenvalues of the Golub-Kahan tridiagonal T_GK (zero
 //      diagonal, off-diagonals d_0, e_0, d_1, e_1, ...; eigenvalues
 //      +-sigma_i) by Sturm-sequence multisection;
 //   c. eigenvectors of T_GK by inverse iteration with partial pivoting; the
 //      entries at odd positions are the left singular vector of B;
-//   d. modified Gram-Schmidt, back-transformation U = H_0 ... H_{p-1} [u; 0],
+//   d. modified Gram-Schmidt (two passes), back-transformation
+//      U = H_0 ... H_{p-1} [u; 0],
 //      and each column signed so that its largest-|.| entry (first on ties)
 //      is positive.
 // Every loop has a fixed iteration bound; nothing waits on other blocks.
@@ -746,16 +747,23 @@ __global__ void __launch_bounds__(kThreads, 2) k_svd_left(const float* __restric
       *reinterpret_cast<float4*>(dst + qr * 36 + 4 * mm) =
           make_float4(z[4 * mm], z[4 * mm + 1], z[4 * mm + 2], z[4 * mm + 3]);
   };
-  if (col == 0) normalise_publish(pub);
-  for (int j = 0; j < r; ++j) {
-    __syncthreads();  // vector j published; reads of the other buffer done
-    if (live && col > j) {
-      float pj[kQ];
-      load32(pub + (j & 1) * kRld, pj);
-      const float d = quad_sum(dot32(pj, z));
+  // Modified Gram-Schmidt, run twice ("twice is enough", Kahan-Parlett):
+  // singular values at the FP32 resolution of K come out of inverse
+  // iteration as nearly parallel vectors, and one pass leaves them orthogonal
+  // only to eps / |residual|.
+  for (int pass = 0; pass < 2; ++pass) {
+    __syncthreads();  // the previous pass's reads of both buffers are done
+    if (col == 0) normalise_publish(pub);
+    for (int j = 0; j < r; ++j) {
+      __syncthreads();  // vector j published; reads of the other buffer done
+      if (live && col > j) {
+        float pj[kQ];
+        load32(pub + (j & 1) * kRld, pj);
+        const float d = quad_sum(dot32(pj, z));
 #pragma unroll
-      for (int kk = 0; kk < kQ; ++kk) z[kk] = fmaf(-d, pj[kk], z[kk]);
-      if (col == j + 1) normalise_publish(pub + ((j + 1) & 1) * kRld);
+        for (int kk = 0; kk < kQ; ++kk) z[kk] = fmaf(-d, pj[kk], z[kk]);
+        if (col == j + 1) normalise_publish(pub + ((j + 1) & 1) * kRld);
+      }
     }
   }
   if (live) {

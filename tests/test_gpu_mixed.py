@@ -164,3 +164,129 @@ def test_unsupported_precision_is_reported(ctx):
     with pytest.raises(B.TNError) as e:
         _run(ctx, [w], 4, B.TN_PREC_BF16)
     assert e.value.status == 8
+
+
+# ------------------------------------------------------ one pass, per edge
+
+def _chain(seed, d, D):
+    from workloads import prng
+    n = len(d)
+    shapes = [(1, d[0], D[0])] + [(D[k - 1], d[k], D[k]) for k in range(1, n - 1)] + \
+             [(D[n - 2], d[n - 1], 1)]
+    blocks, off = [], 0
+    for s in shapes:
+        size = int(np.prod(s))
+        blocks.append((prng.uniform(seed, size, off) - 0.3).reshape(s))
+        off += size
+    return blocks
+
+
+def _isometries(U, d, n):
+    """B_v = U_1 ... U_v as (prod of leaf dims) x r_v matrices."""
+    out = [None] * n
+    Bv = U[1]
+    out[1] = Bv
+    for v in range(2, n - 1):
+        r = U[v].shape[1]
+        Bv = (Bv.reshape(-1, U[v].shape[0] // d[v]) @ U[v].reshape(-1, d[v] * r)).reshape(-1, r)
+        out[v] = Bv
+    return out
+
+
+@pytest.mark.parametrize("d,D,chi", [
+    ([2] * 8, [4, 8, 16, 16, 16, 8, 4], 5),
+    ([2, 3, 2, 4, 2, 2, 3, 2, 2], [6, 12, 20, 24, 24, 20, 12, 6], 7),
+    ([2] * 12, [4, 8, 16, 32, 64, 64, 64, 32, 16, 8, 4], 32),
+])
+def test_tf32_embed_tree_per_edge_matches_oracle(ctx, d, D, chi):
+    """One factored mixed-precision pass (tn_embed_tree, TN_PREC_TF32) on
+    explicit blocks, edge by edge: orthonormal tree tensors, the kept
+    subspaces (projectors of the isometries B_v) where the singular-value gap
+    at the cut resolves them in FP32, the tensor the tree represents and its
+    log-norm, against the FP64 oracle."""
+    n = len(d)
+    n_inst = 3
+    chains = [_chain(200 + i, d, D) for i in range(n_inst)]
+    dev_in = [torch.from_numpy(np.concatenate([b.reshape(-1) for b in ch])).cuda() for ch in chains]
+    r = [d[0]]
+    for k in range(1, n - 1):
+        r.append(min(chi, r[-1] * d[k], D[k], int(np.prod(d[k + 1:]))))
+    sizes = [d[0] * d[1] * r[1]] + [r[k - 1] * d[k] * r[k] for k in range(2, n - 1)] + \
+            [r[n - 2] * d[n - 1]]
+    outs = [torch.full((sum(sizes),), np.nan, dtype=torch.float64, device="cuda")
+            for _ in range(n_inst)]
+    lognorm = torch.zeros(n_inst, dtype=torch.float64, device="cuda")
+    status = torch.full((n_inst,), -1, dtype=torch.int32, device="cuda")
+    ranks = B.tn_embed_tree(ctx, [x.data_ptr() for x in dev_in], d, D, chi,
+                            [o.data_ptr() for o in outs], lognorm.data_ptr(), status.data_ptr(),
+                            precision=B.TN_PREC_TF32,
+                            stream=torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert list(ranks) == r
+    assert status.cpu().tolist() == [0] * n_inst
+    for i, ch in enumerate(chains):
+        blocks = [None, np.einsum("xeb,bfc->efc", ch[0], ch[1])] + ch[2:]
+        tr = []
+        U_ref, Mr_ref, ln_ref = dmtree.density_matrix_alg(blocks, chi, trace=tr)
+        got = outs[i].cpu().numpy()
+        assert np.all(np.isfinite(got))
+        Ug, pos = [None] * n, 0
+        for v in range(1, n - 1):
+            Ug[v] = got[pos:pos + sizes[v - 1]].reshape(U_ref[v].shape)
+            pos += sizes[v - 1]
+            np.testing.assert_allclose(Ug[v].T @ Ug[v], np.eye(Ug[v].shape[1]), atol=2e-6)
+        Mg = got[pos:].reshape(Mr_ref.shape)
+        Bg, Br = _isometries(Ug, d, n), _isometries(U_ref, d, n)
+        gapmin = 1.0  # smallest relative singular-value gap at a cut so far
+        for v in range(1, n - 1):
+            s = np.sqrt(np.maximum(tr[v - 1]["lam"], 0.0))
+            rk = Ug[v].shape[1]
+            if rk < len(s):
+                gapmin = min(gapmin, (s[rk - 1] - s[rk]) / s[0])
+            if gapmin > 1e-3:
+                # Davis-Kahan: subspace error <= backward error / gap, with the
+                # FP32 SVD's backward error a few eps_32 of ||K_v|| (2e-7)
+                np.testing.assert_allclose(Bg[v] @ Bg[v].T, Br[v] @ Br[v].T,
+                                           atol=2e-6 + 2e-7 / gapmin)
+        psi_g = (Bg[n - 2].reshape(-1, Mg.shape[0]) @ Mg).reshape(-1)
+        psi_r = (Br[n - 2].reshape(-1, Mr_ref.shape[0]) @ Mr_ref).reshape(-1)
+        np.testing.assert_allclose(psi_g, psi_r, atol=2e-5)
+        # the mixed path's bar: 1e-6 relative (absolute below a log-norm of 1)
+        assert lognorm[i].item() == pytest.approx(ln_ref, abs=1e-6 * max(1.0, abs(ln_ref)))
+
+
+def test_tf32_embed_tree_on_spin_glass_blocks(ctx):
+    """The factored pass on the blocks of a real row absorption (kept spectrum
+    spanning many decades): the represented tensor and its log-norm."""
+    w = ising.lattice2d(8, 14, 0.7, "gauss", seed=77)
+    trace = []
+    dmtree.partitioned_contract_rows(w, 12, trace=trace)
+    blocks = trace[3]["blocks"]
+    n = len(blocks)
+    b1 = blocks[1]
+    d0 = b1.shape[0]
+    Y = [np.eye(d0).reshape(1, d0, d0), b1.reshape(d0, b1.shape[1], b1.shape[2])] + blocks[2:]
+    d = [y.shape[1] for y in Y]
+    D = [y.shape[2] for y in Y[:-1]]
+    dev_in = torch.from_numpy(np.concatenate([y.reshape(-1) for y in Y])).cuda()
+    out = torch.zeros(1 << 20, dtype=torch.float64, device="cuda")
+    lognorm = torch.zeros(1, dtype=torch.float64, device="cuda")
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    ranks = B.tn_embed_tree(ctx, [dev_in.data_ptr()], d, D, 12, [out.data_ptr()],
+                            lognorm.data_ptr(), status.data_ptr(), precision=B.TN_PREC_TF32,
+                            stream=torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert status.item() == 0
+    U_ref, Mr_ref, ln_ref = dmtree.density_matrix_alg(blocks, 12)
+    got = out.cpu().numpy()
+    pos, Ug = 0, [None] * n
+    for v in range(1, n - 1):
+        size = U_ref[v].shape[0] * ranks[v]
+        Ug[v] = got[pos:pos + size].reshape(U_ref[v].shape)
+        pos += size
+    Mg = got[pos:pos + Mr_ref.size].reshape(Mr_ref.shape)
+    Bg, Br = _isometries(Ug, d, n), _isometries(U_ref, d, n)
+    psi_g = (Bg[n - 2] @ Mg).reshape(-1)
+    psi_r = (Br[n - 2] @ Mr_ref).reshape(-1)
+    np.testing.assert_allclose(psi_g, psi_r, atol=2e-5)
+    assert lognorm.item() == pytest.approx(ln_ref, abs=1e-6 * max(1.0, abs(ln_ref)))
