@@ -66,3 +66,60 @@ CONFIG2 = dict(Lx=32, Ly=32, beta=0.5, couplings="gauss", chis=(32, 64))
 def config2_instance(i: int, Lx: int = 32, Ly: int = 32):
     """Instance i of the 32x32 Gaussian spin glass (seed = 2 * 10**6 + i)."""
     return lattice2d(Lx, Ly, CONFIG2["beta"], "gauss", seed=2 * 10**6 + i)
+
+
+def graph_workload(n: int, edges, J, beta: float):
+    """Ising workload on an arbitrary graph: dict(n, edges, J, beta, tensors)."""
+    edges = np.asarray(edges, dtype=np.int64)
+    return dict(n=n, edges=edges, J=np.asarray(J, dtype=np.float64), beta=beta,
+                tensors=site_tensors(n, edges, np.asarray(J, dtype=np.float64), beta))
+
+
+def cubic(Lx: int, Ly: int, Lz: int, beta: float):
+    """Open Lx x Ly x Lz ferromagnet (J = 1).  Vertex id (x*Ly + y)*Lz + z, so
+    the fibres along z are runs of Lz consecutive ids and a part of k fibres
+    is a run of k*Lz ids (parts taken in id order: a row-wise traversal of the
+    Lx x Ly array of fibres, Sec. 7.3)."""
+    n, edges = graphs.cubic_lattice(Lx, Ly, Lz)
+    w = graph_workload(n, edges, np.ones(len(edges)), beta)
+    w.update(Lx=Lx, Ly=Ly, Lz=Lz)
+    return w
+
+
+def random_regular(n: int, degree: int, beta: float, seed: int):
+    """Random regular graph with J = +-1 (equal probability), vertices
+    renumbered along the recursive-bisection linear ordering (Sec. 7.3), so a
+    part of k tensors is a run of k consecutive ids."""
+    edges = graphs.random_regular(n, degree, seed)
+    edges = graphs.relabel(edges, graphs.bisection_order(n, edges))
+    J = np.where(prng.uniform(seed + 1, len(edges)) < 0.5, 1.0, -1.0)
+    w = graph_workload(n, edges, J, beta)
+    w.update(degree=degree)
+    return w
+
+
+CONFIG3 = dict(L=6, betas=(0.20, 0.2217, 0.25), chis=(16, 32, 64), fibres=(1, 2, 3))
+CONFIG4 = dict(n_inst=256, n_range=(40, 200), degree=3, beta=0.3, chis=(16, 32, 48, 64))
+CONFIG5 = dict(n_range=(100, 300), degree=4, beta=0.25, chi=32)
+
+
+def config4_instance(i: int):
+    """Instance i of the batched random 3-regular workload (seed 4*10**6 + i):
+    n uniform in [40, 200] (rounded up to even), chi uniform in {16, 32, 48, 64}."""
+    seed = 4 * 10**6 + i
+    lo, hi = CONFIG4["n_range"]
+    n = int(prng.randint(seed, 1, lo, hi, offset=0)[0])
+    n += n % 2
+    chi = int(CONFIG4["chis"][int(prng.randint(seed, 1, 0, 3, offset=1)[0])])
+    w = random_regular(n, CONFIG4["degree"], CONFIG4["beta"], seed)
+    w.update(chi=chi)
+    return w
+
+
+def config5_instance(i: int):
+    """Instance i of the random 4-regular workload (seed 5*10**6 + i):
+    n uniform in [100, 300]."""
+    seed = 5 * 10**6 + i
+    lo, hi = CONFIG5["n_range"]
+    n = int(prng.randint(seed, 1, lo, hi, offset=0)[0])
+    return random_regular(n, CONFIG5["degree"], CONFIG5["beta"], seed)
