@@ -97,7 +97,11 @@ typedef struct {
                                (maximally unbalanced path), or NULL = 0..N-1  */
   int32_t n_path;
   int32_t ansatz;           /* 0 = MPS embedding tree (App. C); others: UNSUPPORTED */
-  int32_t swap_batch;       /* swap batch size r of Algorithm approx_tensor_network */
+  int32_t swap_batch;       /* swap batch size r of Algorithm approx_tensor_network
+                               (<= 0: one density-matrix pass per contraction)  */
+  int32_t planner;          /* 0: boundary absorption when every part fits it
+                               (see tn_plan), else the general planner;
+                               1: always the general planner                  */
 } tn_plan_opts;
 
 typedef struct tn_plan tn_plan_t;
@@ -124,7 +128,24 @@ typedef struct {
   double flops_kfactor;     /* K_v = M_v C_v                                   */
   double flops_svd;         /* Golub-Kahan bidiagonalisation of K_v + the
                                back-transformation of the r_v kept vectors    */
+  int32_t n_exec_steps;     /* executed steps (tn_plan_step_query): the DM
+                               passes, the closing contraction and, for
+                               boundary plans, the exact first part          */
+  int32_t general;          /* 1 if the general planner built the plan        */
 } tn_plan_info;
+
+/* One executed step of a plan (host).                                        */
+typedef struct {
+  int32_t kind;             /* 0 exact first part, 1 density-matrix pass,
+                               2 closing contraction                           */
+  int32_t n;                /* leaves of the pass's MPS tree (kind 1), chain
+                               positions (kinds 0 and 2)                       */
+  int32_t n_kt;             /* Kendall-Tau distance between the reference and
+                               the constraint-tree ordering of the contraction
+                               this pass belongs to (general plans, else 0)    */
+  int32_t general;          /* 1 if the block of every position is a gather of
+                               the tensors embedded there (general planner)   */
+} tn_plan_step;
 
 /* ---------------------------------------------------------------- planning
  * Build the host-side plan of Algorithm partitioned_contract for one graph:
@@ -142,6 +163,14 @@ typedef struct {
 tn_status tn_plan(const tn_graph* graph, const tn_plan_opts* opts, tn_plan_t** out);
 tn_status tn_plan_destroy(tn_plan_t* plan);
 tn_status tn_plan_query(const tn_plan_t* plan, tn_plan_info* info);
+/* Shape of executed step `step` (0 .. n_exec_steps-1).  Every output array
+ * is optional (NULL skips it) and host memory of the caller:
+ *   leaves[n]: graph edge id of every leaf in tree order (kind 1; general
+ *              plans; -1 otherwise), d[n] leaf dims, D[n] untruncated
+ *              tree-edge dims (D[n-1] = 1), r[n-1] ranks after the pass
+ *              (kind 1 only).                                                */
+tn_status tn_plan_step_query(const tn_plan_t* plan, int32_t step, tn_plan_step* info,
+                             int32_t* leaves, int32_t* d, int32_t* D, int32_t* r);
 /* Offset (in doubles) of vertex v's tensor inside a packed site buffer.    */
 tn_status tn_plan_site_offset(const tn_plan_t* plan, int32_t vertex, int64_t* offset);
 

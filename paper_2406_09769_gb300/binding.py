@@ -32,7 +32,8 @@ class tn_graph(ctypes.Structure):
 class tn_plan_opts(ctypes.Structure):
     _fields_ = [("chi_max", ctypes.c_int32), ("env_size", ctypes.c_int32),
                 ("partition", _i32p), ("path", _i32p), ("n_path", ctypes.c_int32),
-                ("ansatz", ctypes.c_int32), ("swap_batch", ctypes.c_int32)]
+                ("ansatz", ctypes.c_int32), ("swap_batch", ctypes.c_int32),
+                ("planner", ctypes.c_int32)]
 
 
 class tn_plan_info(ctypes.Structure):
@@ -43,7 +44,13 @@ class tn_plan_info(ctypes.Structure):
                 ("flops_density", ctypes.c_double), ("flops_project", ctypes.c_double),
                 ("flops_eig", ctypes.c_double), ("n_eig", ctypes.c_int64),
                 ("flops_factor", ctypes.c_double), ("flops_kfactor", ctypes.c_double),
-                ("flops_svd", ctypes.c_double)]
+                ("flops_svd", ctypes.c_double), ("n_exec_steps", ctypes.c_int32),
+                ("general", ctypes.c_int32)]
+
+
+class tn_plan_step(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n", ctypes.c_int32), ("n_kt", ctypes.c_int32),
+                ("general", ctypes.c_int32)]
 
 
 class TNError(RuntimeError):
@@ -55,7 +62,8 @@ class TNError(RuntimeError):
 _lib = None
 
 # Every symbol include/tn_dmtree.h declares.
-EXPORTS = ("tn_plan", "tn_plan_destroy", "tn_plan_query", "tn_plan_site_offset",
+EXPORTS = ("tn_plan", "tn_plan_destroy", "tn_plan_query", "tn_plan_step_query",
+           "tn_plan_site_offset",
            "tn_ctx_create", "tn_ctx_destroy", "tn_embed_tree", "tn_contract_approx",
            "tn_logz", "tn_contract_approx_host", "tn_embed_tree_noalloc",
            "tn_rank_model_params", "tn_rank_model_load", "tn_rank_record", "tn_rank_labels",
@@ -81,6 +89,8 @@ def lib():
     L.tn_plan_destroy.argtypes = [_vp]
     L.tn_plan_query.argtypes = [_vp, ctypes.POINTER(tn_plan_info)]
     L.tn_plan_site_offset.argtypes = [_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]
+    L.tn_plan_step_query.argtypes = [_vp, ctypes.c_int32, ctypes.POINTER(tn_plan_step), _i32p,
+                                     _i32p, _i32p, _i32p]
     L.tn_ctx_create.argtypes = [ctypes.c_int32, ctypes.POINTER(_vp)]
     L.tn_ctx_destroy.argtypes = [_vp]
     L.tn_embed_tree.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _i32p, _i32p,
@@ -176,7 +186,7 @@ class Ctx:
 
 
 def tn_plan(n_vertices, edges, edge_dim, chi, env_size=0, partition=None, path=None,
-            ansatz=0, swap_batch=32):
+            ansatz=0, swap_batch=32, planner=0):
     edges = np.asarray(edges).reshape(-1, 2)
     u, up = _i32(edges[:, 0])
     v, vp = _i32(edges[:, 1])
@@ -192,7 +202,8 @@ def tn_plan(n_vertices, edges, edge_dim, chi, env_size=0, partition=None, path=N
         pt, path_p = _i32(path)
         keep.append(pt)
         n_path = len(pt)
-    o = tn_plan_opts(int(chi), int(env_size), part_p, path_p, n_path, int(ansatz), int(swap_batch))
+    o = tn_plan_opts(int(chi), int(env_size), part_p, path_p, n_path, int(ansatz), int(swap_batch),
+                     int(planner))
     h = _vp()
     _check(lib().tn_plan(ctypes.byref(g), ctypes.byref(o), ctypes.byref(h)))
     return Plan(h, None)
@@ -202,6 +213,29 @@ def tn_plan_query(plan):
     info = tn_plan_info()
     _check(lib().tn_plan_query(plan.handle, ctypes.byref(info)))
     return {k: getattr(info, k) for k, _ in tn_plan_info._fields_}
+
+
+def tn_plan_step_query(plan, step):
+    """dict(kind, n, n_kt, general, leaves, d, D, r) of executed step `step`."""
+    info = tn_plan_step()
+    _check(lib().tn_plan_step_query(plan.handle, int(step), ctypes.byref(info), None, None, None,
+                                    None))
+    n = info.n
+    leaves = np.zeros(n, np.int32)
+    d = np.zeros(n, np.int32)
+    D = np.zeros(n, np.int32)
+    r = np.zeros(max(n - 1, 1), np.int32)
+    ptr = lambda a: a.ctypes.data_as(_i32p)
+    _check(lib().tn_plan_step_query(plan.handle, int(step), ctypes.byref(info), ptr(leaves),
+                                    ptr(d), ptr(D), ptr(r)))
+    return dict(kind=info.kind, n=n, n_kt=info.n_kt, general=info.general,
+                leaves=leaves.tolist(), d=d.tolist(), D=D.tolist(),
+                r=r[:n - 1].tolist() if info.kind == 1 else [])
+
+
+def tn_plan_steps(plan):
+    """Every executed step of a plan (tn_plan_step_query in order)."""
+    return [tn_plan_step_query(plan, s) for s in range(tn_plan_query(plan)["n_exec_steps"])]
 
 
 def tn_plan_site_offset(plan, vertex):

@@ -15,8 +15,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtn_dmtree.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["kernels_fp64.cu", "kernels_f32.cu", "eigh.cu", "svd.cu", "tc_gemm.cu",
-              "learned.cu", "peaks.cu", "api.cu"]
-CPP_SOURCES = ["planner.cpp"]
+              "learned.cu", "peaks.cu", "gather.cu", "api.cu"]
+CPP_SOURCES = ["planner.cpp", "planner_graph.cpp"]
 
 
 def _nvcc():

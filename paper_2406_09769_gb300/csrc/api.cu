@@ -132,13 +132,14 @@ namespace {
 
 struct Ws {
   // per-instance strides (elements) and base pointers
-  long long sS, sY, sR, sX, sM, sL, sP, sLam, sAmax, sInv;
-  double *S0, *S1, *Y, *R, *X, *M, *G, *L, *P, *lam, *inv;
+  long long sS, sY, sR, sX, sM, sL, sP, sLam, sAmax, sInv, sScr;
+  double *S0, *S1, *Y, *R, *X, *M, *G, *L, *P, *lam, *inv, *scr;
   unsigned long long* amax;
 };
 
 struct Dims {
-  long long maxS = 1, maxY = 1, maxR = 1, maxX = 1, maxM = 1, maxL = 1, maxP = 1, maxLam = 1;
+  long long maxS = 1, maxY = 1, maxR = 1, maxX = 1, maxM = 1, maxL = 1, maxP = 1, maxLam = 1,
+            maxScr = 1;
   int maxN = 1, maxD = 1;
 };
 
@@ -148,6 +149,7 @@ Dims plan_dims(const tn_plan_t* P) {
     d.maxS = std::max<long long>(d.maxS, st.s_total);
     d.maxY = std::max<long long>(d.maxY, st.y_total);
     d.maxR = std::max<long long>(d.maxR, st.r_total);
+    d.maxScr = std::max<long long>(d.maxScr, st.scratch_elems);
     d.maxN = std::max(d.maxN, st.n);
     for (int k = 0; k < st.n; ++k) {
       d.maxD = std::max(d.maxD, st.D[k]);
@@ -175,22 +177,25 @@ Ws carve(tn_ctx* c, const Dims& d, int B, int nv, bool dry = false, size_t* byte
   Ws w{};
   w.sS = d.maxS; w.sY = d.maxY; w.sR = d.maxR; w.sX = d.maxX; w.sM = d.maxM;
   w.sL = d.maxL; w.sP = d.maxP; w.sLam = d.maxLam; w.sAmax = d.maxN; w.sInv = nv;
+  w.sScr = d.maxScr;
   const size_t dbl = sizeof(double);
   size_t off[16];
   size_t tot = 0;
-  const long long sizes[] = {w.sS, w.sS, w.sY, w.sR, w.sX, w.sM, w.sM, w.sL, w.sP, w.sLam, w.sInv};
-  for (int i = 0; i < 11; ++i) {
+  const long long sizes[] = {w.sS, w.sS, w.sY, w.sR, w.sX, w.sM, w.sM, w.sL, w.sP, w.sLam, w.sInv,
+                             w.sScr};
+  for (int i = 0; i < 12; ++i) {
     off[i] = tot;
     tot += align256(dbl * size_t(sizes[i]) * B);
   }
-  off[11] = tot;
+  off[12] = tot;
   tot += align256(sizeof(unsigned long long) * size_t(w.sAmax) * B);
   if (bytes) *bytes = tot;
   if (dry) return w;
   char* base = at ? at : static_cast<char*>(c->arena.get(tot));
-  double** outs[] = {&w.S0, &w.S1, &w.Y, &w.R, &w.X, &w.M, &w.G, &w.L, &w.P, &w.lam, &w.inv};
-  for (int i = 0; i < 11; ++i) *outs[i] = reinterpret_cast<double*>(base + off[i]);
-  w.amax = reinterpret_cast<unsigned long long*>(base + off[11]);
+  double** outs[] = {&w.S0, &w.S1, &w.Y, &w.R, &w.X, &w.M, &w.G, &w.L, &w.P, &w.lam, &w.inv,
+                     &w.scr};
+  for (int i = 0; i < 12; ++i) *outs[i] = reinterpret_cast<double*>(base + off[i]);
+  w.amax = reinterpret_cast<unsigned long long*>(base + off[12]);
   return w;
 }
 
@@ -295,7 +300,19 @@ struct StepTables {
   int64_t* y_off;
   int32_t* D;      // n + 1 entries (last = max D)
   int64_t* r_off;  // memoised density matrix R_k offsets (n entries)
+  // general plans: the block programs (ops by level, operands, code, prefix)
+  tn::GOp* gop;
+  tn::GTen* gten;
+  int32_t* gcode;
+  int64_t* gpre;
 };
+
+size_t general_bytes(const tn::Step& st) {
+  if (!st.general) return 0;
+  return align256(sizeof(tn::GOp) * st.gop.size()) + align256(sizeof(tn::GTen) * st.gten.size()) +
+         align256(sizeof(int32_t) * st.gcode.size()) +
+         align256(sizeof(int64_t) * (st.gop.size() + 1));
+}
 
 // Device copies of one bucket's per-step tables: [tens ptrs B][site_off nv]
 // [site_len nv] then per step fuse / y_off / D / r_off.
@@ -305,7 +322,7 @@ size_t tables_bytes(const tn_plan_t* P, int B) {
   for (size_t s = 0; s < P->steps.size(); ++s) {
     const int n = P->steps[s].n;
     tot += align256(sizeof(tn::FuseSite) * n) + 2 * align256(sizeof(int64_t) * n) +
-           align256(sizeof(int32_t) * (n + 1));
+           align256(sizeof(int32_t) * (n + 1)) + general_bytes(P->steps[s]);
   }
   return tot;
 }
@@ -341,7 +358,7 @@ std::vector<StepTables> fill_tables(const tn_plan_t* P, const std::vector<Lay>& 
         f.dhl = op.dhl; f.dhr = op.dhr; f.de = op.de;
         f.t_off = op.t_off; f.sp = op.sp; f.shl = op.shl; f.shr = op.shr; f.se = op.se;
         f.y_off = (stp.kind == 0) ? lay[s].s_off[k] : lay[s].y_off[k];
-        f.s_off = (s > 0) ? lay[s - 1].s_off[k] : 0;
+        f.s_off = (s > 0 && !stp.general) ? lay[s - 1].s_off[k] : 0;
         fh[k] = f;
       }
     }
@@ -365,6 +382,57 @@ std::vector<StepTables> fill_tables(const tn_plan_t* P, const std::vector<Lay>& 
     }
     out[s].r_off = reinterpret_cast<int64_t*>(dbase + q);
     q += align256(sizeof(int64_t) * n);
+    out[s].gop = nullptr;
+    out[s].gten = nullptr;
+    out[s].gcode = nullptr;
+    out[s].gpre = nullptr;
+    if (stp.general) {
+      const size_t nop = stp.gop.size(), nten = stp.gten.size(), ncode = stp.gcode.size();
+      out[s].gop = reinterpret_cast<tn::GOp*>(dbase + q);
+      if (h) {
+        tn::GOp* gh = reinterpret_cast<tn::GOp*>(h + q);
+        for (size_t i = 0; i < nop; ++i) {
+          const tn::GOpH& x = stp.gop[i];
+          tn::GOp g{};
+          g.dst_off = x.to_block ? lay[s].y_off[x.pos] : x.dst_off;
+          g.n_elems = x.n_elems;
+          g.to_block = x.to_block; g.Dl = x.Dl; g.dkDr = x.dkDr;
+          g.ns = x.ns; g.nout = x.nout; g.nsum = x.nsum; g.nt = x.nt;
+          g.t_first = x.t_first; g.code_off = x.code_off;
+          gh[i] = g;
+        }
+      }
+      q += align256(sizeof(tn::GOp) * nop);
+      out[s].gten = reinterpret_cast<tn::GTen*>(dbase + q);
+      if (h) {
+        tn::GTen* th = reinterpret_cast<tn::GTen*>(h + q);
+        for (size_t i = 0; i < nten; ++i) {
+          const tn::GTensorH& x = stp.gten[i];
+          tn::GTen g{};
+          g.src = x.src; g.nleg = x.nleg; g.leg_off = x.leg_off;
+          if (x.src == 0) {
+            g.base = P->site_off[x.id];
+            g.vertex = x.id;
+          } else if (x.src == 1) {
+            g.base = lay[s - 1].s_off[x.id];
+          } else {
+            g.base = x.id;
+          }
+          th[i] = g;
+        }
+      }
+      q += align256(sizeof(tn::GTen) * nten);
+      out[s].gcode = reinterpret_cast<int32_t*>(dbase + q);
+      if (h) std::memcpy(h + q, stp.gcode.data(), sizeof(int32_t) * ncode);
+      q += align256(sizeof(int32_t) * ncode);
+      out[s].gpre = reinterpret_cast<int64_t*>(dbase + q);
+      if (h) {
+        int64_t* ph = reinterpret_cast<int64_t*>(h + q);
+        ph[0] = 0;
+        for (size_t i = 0; i < nop; ++i) ph[i + 1] = ph[i] + stp.gop[i].n_elems;
+      }
+      q += align256(sizeof(int64_t) * (nop + 1));
+    }
     o = q;
   }
   return out;
@@ -534,6 +602,22 @@ void dm_pass(tn_ctx* c, const tn::Step& st, const Ws& w, double* Snext, int B, i
      "root launch");
 }
 
+// Blocks of a general step: its gather-contraction programs, level by level.
+template <typename TS, typename TY>
+void gather_blocks(tn_ctx* c, const tn::Step& st, const StepTables& tab, const double** tens,
+                   const double* inv, long long sInv, const TS* Scur, long long sS, double* scr,
+                   long long sScr, TY* Y, long long sY, TY* Yt, int B, cudaStream_t strm) {
+  std::vector<int64_t> pre(st.gop.size() + 1, 0);
+  for (size_t i = 0; i < st.gop.size(); ++i) pre[i + 1] = pre[i] + st.gop[i].n_elems;
+  for (size_t j = 0; j + 1 < st.level_start.size(); ++j) {
+    const int a = st.level_start[j], b = st.level_start[j + 1];
+    Scope(c, TN_KC_FUSE, strm),
+    ck(tn::launch_gather<TS, TY>(tab.gop, tab.gten, tab.gcode, tab.gpre, a, b, pre[b] - pre[a],
+                                 tens, inv, sInv, Scur, sS, scr, sScr, Y, sY, Yt, B, strm),
+       "gather");
+  }
+}
+
 // FP64 path of one bucket (tables in place, results at c->logz etc.).
 void run_plan(tn_ctx* c, const Bucket& bk, int precision, bool learned, cudaStream_t strm) {
   const tn_plan_t* P = bk.P;
@@ -553,6 +637,23 @@ void run_plan(tn_ctx* c, const Bucket& bk, int precision, bool learned, cudaStre
   double* Snext = w.S1;
   for (size_t s = 0; s < P->steps.size(); ++s) {
     const tn::Step& st = P->steps[s];
+    if (st.general) {
+      gather_blocks<double, double>(c, st, tabs[s], tens_table, w.inv, w.sInv, Scur, w.sS, w.scr,
+                                    w.sScr, w.Y, w.sY, nullptr, B, strm);
+      if (st.kind == 1) {
+        const PassCtx pc = learn_pass(ls, c, st);
+        dm_pass(c, st, w, Snext, B, precision, strm, &pc);
+        std::swap(Scur, Snext);
+      } else {
+        int maxD = 1;
+        for (int k = 0; k < st.n; ++k) maxD = std::max(maxD, st.D[k]);
+        Scope(c, TN_KC_CLOSE, strm),
+        ck(tn::launch_close(w.Y, w.sY, tabs[s].y_off, tabs[s].D, st.n, maxD, c->logscale, c->logz,
+                            c->status, B, strm),
+           "close");
+      }
+      continue;
+    }
     int maxe = 1;
     for (int k = 0; k < st.n; ++k) {
       const tn::SiteOp& o = st.site[k];
@@ -593,19 +694,20 @@ void run_plan(tn_ctx* c, const Bucket& bk, int precision, bool learned, cudaStre
 // compensated 3-term TF32 split; FP32 eigensolver; root norm, log-scale and
 // closing contraction accumulated in FP64.
 struct WsF {
-  long long sS, sY, sR, sX, sM, sL, sP, sUt, sLam, sAmax, sInv;
+  long long sS, sY, sR, sX, sM, sL, sP, sUt, sLam, sAmax, sInv, sScr;
   float *S0, *S1, *Y, *Yt, *R, *X, *M, *Mt, *G, *L, *P, *Ut;
-  double *lam, *inv;
+  double *lam, *inv, *scr;
   unsigned int* amax;
 };
 
 WsF carve_f32(tn_ctx* c, const tn_plan_t* P, const std::vector<Lay>& lay, int B,
               bool dry = false, size_t* bytes = nullptr, char* at = nullptr) {
   long long maxS = 4, maxY = 4, maxR = 4, maxX = 4, maxM = 4, maxL = 4, maxP = 4, maxUt = 4,
-            maxLam = 1;
+            maxLam = 1, maxScr = 1;
   int maxN = 1;
   for (size_t s = 0; s < P->steps.size(); ++s) {
     const tn::Step& st = P->steps[s];
+    maxScr = std::max<long long>(maxScr, st.scratch_elems);
     maxS = std::max<long long>(maxS, lay[s].s_total);
     maxY = std::max<long long>(maxY, lay[s].y_total);
     maxR = std::max<long long>(maxR, lay[s].r_total);
@@ -626,7 +728,7 @@ WsF carve_f32(tn_ctx* c, const tn_plan_t* P, const std::vector<Lay>& lay, int B,
   }
   WsF w{};
   w.sS = maxS; w.sY = maxY; w.sR = maxR; w.sX = maxX; w.sM = maxM; w.sL = maxL; w.sP = maxP;
-  w.sUt = maxUt; w.sLam = maxLam; w.sAmax = maxN; w.sInv = P->n_vertices;
+  w.sUt = maxUt; w.sLam = maxLam; w.sAmax = maxN; w.sInv = P->n_vertices; w.sScr = maxScr;
   const long long fsz[] = {w.sS, w.sS, w.sY, w.sY, w.sR, w.sX, w.sM, w.sM, w.sM, w.sL, w.sP, w.sUt};
   float** fout[] = {&w.S0, &w.S1, &w.Y, &w.Yt, &w.R, &w.X, &w.M, &w.Mt, &w.G, &w.L, &w.P, &w.Ut};
   size_t off[16], tot = 0;
@@ -639,6 +741,8 @@ WsF carve_f32(tn_ctx* c, const tn_plan_t* P, const std::vector<Lay>& lay, int B,
   off[13] = tot;
   tot += align256(sizeof(double) * size_t(w.sInv) * B);
   off[14] = tot;
+  tot += align256(sizeof(double) * size_t(w.sScr) * B);
+  off[15] = tot;
   tot += align256(sizeof(unsigned int) * size_t(w.sAmax) * B);
   if (bytes) *bytes = tot;
   if (dry) return w;
@@ -646,7 +750,8 @@ WsF carve_f32(tn_ctx* c, const tn_plan_t* P, const std::vector<Lay>& lay, int B,
   for (int i = 0; i < 12; ++i) *fout[i] = reinterpret_cast<float*>(base + off[i]);
   w.lam = reinterpret_cast<double*>(base + off[12]);
   w.inv = reinterpret_cast<double*>(base + off[13]);
-  w.amax = reinterpret_cast<unsigned int*>(base + off[14]);
+  w.scr = reinterpret_cast<double*>(base + off[14]);
+  w.amax = reinterpret_cast<unsigned int*>(base + off[15]);
   return w;
 }
 
@@ -817,6 +922,23 @@ void run_plan_tc(tn_ctx* c, const Bucket& bk, int sub_split, bool factored, bool
   float* Snext = w.S1;
   for (size_t s = 0; s < P->steps.size(); ++s) {
     const tn::Step& st = P->steps[s];
+    if (st.general) {
+      gather_blocks<float, float>(c, st, tabs[s], tens_table, w.inv, w.sInv, Scur, w.sS, w.scr,
+                                  w.sScr, w.Y, w.sY, st.kind == 1 ? w.Yt : nullptr, B, strm);
+      if (st.kind == 1) {
+        const PassCtx pc = learn_pass(ls, c, st);
+        dm_pass_tc(c, st, lay[s], w, Snext, B, sub_split, factored, &tabs[s], strm, &pc);
+        std::swap(Scur, Snext);
+      } else {
+        int maxD = 1;
+        for (int k = 0; k < st.n; ++k) maxD = std::max(maxD, st.D[k]);
+        Scope(c, TN_KC_CLOSE, strm),
+        ck(tn::launch_close_f32(w.Y, w.sY, tabs[s].y_off, tabs[s].D, st.n, maxD, c->logscale,
+                                c->logz, c->status, B, strm),
+           "close");
+      }
+      continue;
+    }
     int maxe = 1, maxdl = 1, maxj = 1, maxt = 1, maxa = 1, maxb = 1, other = 0;
     for (int k = 0; k < st.n; ++k) {
       const tn::SiteOp& o = st.site[k];

@@ -173,6 +173,31 @@ bool svd_left_supported(int m, int n, int r);
 size_t svd_left_smem_bytes(int m, int n, int r);
 cudaError_t svd_configure();
 
+// Blocks of general plans (gather.cu).  One op of a chain position's program
+// (device copy of GOpH with resolved offsets): out[e] = sum over the summed
+// slots of the product of its operands, e decoded row-major into the output
+// slots (a slot listed twice must take equal digits, else 0).  Output: the
+// block (y_off into Y and, if Yt is set, its transpose (dkDr x Dl) into Yt)
+// or scratch at dst_off.
+struct GOp {
+  int64_t dst_off, n_elems;
+  int32_t to_block, Dl, dkDr, ns, nout, nsum, nt, t_first, code_off, pad;
+};
+// An operand: src 0 = raw site tensor (tens[i] + base, times inv[vertex]),
+// 1 = MPS site of the previous step (S + base), 2 = scratch (scr + base).
+struct GTen {
+  int64_t base;
+  int32_t src, vertex, nleg, leg_off;
+};
+// Runs ops [a, b) of one level; pre: exclusive prefix of n_elems over all ops
+// of the step (pre[i] .. pre[i+1] are op i's elements).
+template <typename TS, typename TY>
+cudaError_t launch_gather(const GOp* ops, const GTen* ten, const int32_t* code, const int64_t* pre,
+                          int a, int b, int64_t n_elems, const double* const* tens,
+                          const double* inv, long long sInv, const TS* S, long long sS,
+                          double* scr, long long sScr, TY* Y, long long sY, TY* Yt, int batch,
+                          cudaStream_t st);
+
 template <typename T>
 size_t eigh_smem_bytes(int n, int r, int nlam);
 template <typename T>

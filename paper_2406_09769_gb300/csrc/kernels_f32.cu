@@ -484,6 +484,11 @@ cudaError_t launch_close_f32(const float* Y, long long sY, const int64_t* y_off,
                              int n, int maxD, const double* logscale, double* logz, int* status,
                              int batch, cudaStream_t st) {
   const size_t smem = sizeof(double) * size_t(2 * maxD);
+  if (smem > 48 * 1024) {  // wide closing chains of general plans (maxD <= 4096)
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_close_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+  }
   k_close_f32<<<batch, 256, smem, st>>>(Y, sY, y_off, D, n, logscale, logz, status);
   return cudaGetLastError();
 }

@@ -316,6 +316,11 @@ cudaError_t launch_close(const double* Y, long long sY, const int64_t* y_off, co
                          int n, int maxD, const double* logscale, double* logz, int* status,
                          int batch, cudaStream_t st) {
   const size_t smem = sizeof(double) * size_t(2 * maxD);
+  if (smem > 48 * 1024) {  // wide closing chains of general plans (maxD <= 4096)
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_close, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+  }
   k_close<<<batch, 256, smem, st>>>(Y, sY, y_off, D, n, logscale, logz, status);
   return cudaGetLastError();
 }

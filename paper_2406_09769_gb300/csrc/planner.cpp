@@ -45,9 +45,29 @@ bool plans_equivalent(const tn_plan_t* a, const tn_plan_t* b) {
   for (size_t s = 0; s < a->steps.size(); ++s) {
     const Step& x = a->steps[s];
     const Step& y = b->steps[s];
-    if (x.kind != y.kind || x.n != y.n || x.d != y.d || x.D != y.D || x.r != y.r) return false;
+    if (x.kind != y.kind || x.n != y.n || x.d != y.d || x.D != y.D || x.r != y.r ||
+        x.general != y.general)
+      return false;
     for (int k = 0; k < x.n; ++k)
       if (!same_ops(x.site[k], y.site[k])) return false;
+    if (x.general) {
+      if (x.gcode != y.gcode || x.gten.size() != y.gten.size() || x.gop.size() != y.gop.size() ||
+          x.level_start != y.level_start || x.scratch_elems != y.scratch_elems)
+        return false;
+      for (size_t i = 0; i < x.gop.size(); ++i) {
+        const GOpH &p = x.gop[i], &q = y.gop[i];
+        if (p.pos != q.pos || p.level != q.level || p.to_block != q.to_block ||
+            p.dst_off != q.dst_off || p.n_elems != q.n_elems || p.Dl != q.Dl ||
+            p.dkDr != q.dkDr || p.ns != q.ns || p.nout != q.nout || p.nsum != q.nsum ||
+            p.nt != q.nt || p.t_first != q.t_first || p.code_off != q.code_off)
+          return false;
+      }
+      for (size_t i = 0; i < x.gten.size(); ++i) {
+        const GTensorH &p = x.gten[i], &q = y.gten[i];
+        if (p.src != q.src || p.id != q.id || p.nleg != q.nleg || p.leg_off != q.leg_off)
+          return false;
+      }
+    }
   }
   return true;
 }
@@ -58,10 +78,7 @@ using tn::set_error;
 
 namespace {
 
-struct Fail {
-  tn_status st;
-  std::string msg;
-};
+using Fail = tn::PlanFail;
 
 [[noreturn]] void fail(tn_status st, const std::string& msg) { throw Fail{st, msg}; }
 
@@ -72,7 +89,9 @@ int64_t cap_mul(int64_t a, int64_t b) {
   return p > CAP ? CAP : p;
 }
 
-void layouts(tn::Step& st) {
+}  // namespace
+
+void tn::step_layouts(tn::Step& st) {
   const int n = st.n;
   st.y_off.assign(n, 0);
   int64_t off = 0;
@@ -113,6 +132,12 @@ void layouts(tn::Step& st) {
   }
   st.r_total = off;
 }
+
+namespace {
+
+void boundary_steps(const tn_graph* g, const tn_plan_opts* o, tn_plan_t* P,
+                    const std::vector<std::vector<int>>& members, const std::vector<int>& path,
+                    const std::vector<std::vector<int>>& inc);
 
 void build(const tn_graph* g, const tn_plan_opts* o, tn_plan_t* P) {
   if (!g || !o) fail(TN_ERR_INVALID, "graph and opts must be non-NULL");
@@ -185,6 +210,33 @@ void build(const tn_graph* g, const tn_plan_opts* o, tn_plan_t* P) {
     off += len;
   }
   P->site_elems = off;
+  if (o->planner < 0 || o->planner > 1) fail(TN_ERR_INVALID, "planner must be 0 or 1");
+  bool general = o->planner == 1;
+  if (!general) {
+    try {
+      boundary_steps(g, o, P, members, path, inc);
+      P->n_contractions = nparts - 1;
+    } catch (const Fail& f) {
+      if (f.st != TN_ERR_UNSUPPORTED) throw;
+      general = true;
+      P->steps.clear();
+    }
+  }
+  if (general) {
+    std::vector<std::vector<int>> parts;
+    for (int s = 0; s < nparts; ++s) parts.push_back(members[path[s]]);
+    tn::build_general_steps(g, o, parts, P);
+  }
+  tn::plan_info(P);
+}
+
+// Boundary absorption: every part a simple path whose i-th vertex absorbs the
+// i-th open leg of the intermediate (the 2D lattice rows).
+void boundary_steps(const tn_graph* g, const tn_plan_opts* o, tn_plan_t* P,
+                    const std::vector<std::vector<int>>& members, const std::vector<int>& path,
+                    const std::vector<std::vector<int>>& inc) {
+  const int nv = g->n_vertices;
+  const int nparts = int(members.size());
   auto other = [&](int e, int v) { return g->edge_u[e] == v ? g->edge_v[e] : g->edge_u[e]; };
   auto stride_of = [&](int v, int e) {
     int64_t s = 1;
@@ -195,7 +247,6 @@ void build(const tn_graph* g, const tn_plan_opts* o, tn_plan_t* P) {
     }
     return int64_t(-1);
   };
-
   std::vector<char> absorbed(nv, 0);
   std::vector<int> legs;                          // open legs of the intermediate (edge ids)
   std::vector<int64_t> sa, sd, sb;                // boundary site shapes (a, d, b)
@@ -337,15 +388,22 @@ void build(const tn_graph* g, const tn_plan_opts* o, tn_plan_t* P) {
         sb[k] = (k == m - 1) ? 1 : st.r[k];
       }
     }
-    layouts(st);
+    tn::step_layouts(st);
     P->steps.push_back(std::move(st));
     for (int u : mem) absorbed[u] = 1;
     legs = new_legs;
   }
-  // info and flop counts (Sec. 2.2 cost model, 2 flops per multiply-add)
+}
+
+}  // namespace
+
+// Plan summary and flop counts (Sec. 2.2 cost model, 2 flops per multiply-add).
+void tn::plan_info(tn_plan_t* P) {
   tn_plan_info& I = P->info;
   std::memset(&I, 0, sizeof(I));
-  I.n_steps = nparts - 1;
+  I.n_steps = P->n_contractions;
+  I.n_exec_steps = int32_t(P->steps.size());
+  I.general = (!P->steps.empty() && P->steps.back().general) ? 1 : 0;
   I.site_elems = P->site_elems;
   for (const tn::Step& st : P->steps) {
     I.max_legs = std::max(I.max_legs, st.n);
@@ -376,8 +434,6 @@ void build(const tn_graph* g, const tn_plan_opts* o, tn_plan_t* P) {
     I.flops_project += 2.0 * st.r[n - 2] * st.D[n - 2] * st.d[n - 1];
   }
 }
-
-}  // namespace
 
 extern "C" tn_status tn_plan(const tn_graph* graph, const tn_plan_opts* opts, tn_plan_t** out) {
   if (!out) {
@@ -420,6 +476,28 @@ extern "C" tn_status tn_plan_query(const tn_plan_t* plan, tn_plan_info* info) {
     return TN_ERR_INVALID;
   }
   *info = plan->info;
+  return TN_OK;
+}
+
+extern "C" tn_status tn_plan_step_query(const tn_plan_t* plan, int32_t step, tn_plan_step* info,
+                                        int32_t* leaves, int32_t* d, int32_t* D, int32_t* r) {
+  if (!plan || step < 0 || step >= int32_t(plan->steps.size())) {
+    set_error("tn_plan_step_query: invalid argument");
+    return TN_ERR_INVALID;
+  }
+  const tn::Step& st = plan->steps[step];
+  if (info) {
+    info->kind = st.kind;
+    info->n = st.n;
+    info->n_kt = st.n_kt;
+    info->general = st.general ? 1 : 0;
+  }
+  for (int k = 0; k < st.n; ++k) {
+    if (leaves) leaves[k] = (st.general && st.kind == 1) ? st.leaves[k] : -1;
+    if (d) d[k] = st.d[k];
+    if (D) D[k] = st.D[k];
+    if (r && st.kind == 1 && k + 1 < st.n) r[k] = st.r[k];
+  }
   return TN_OK;
 }
 
