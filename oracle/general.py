@@ -483,6 +483,38 @@ def plan(n, edges, dims, parts, chi, swap_batch=0):
 
 # ------------------------------------------------------------ the contraction
 
+def _contract_pairwise(ops, out):
+    """Contraction of the operands ops = [array, labels, array, labels, ...]
+    into the labels ``out`` by repeated pairwise tensordot: the pair sharing
+    a label whose result is smallest first (an outer product only when no pair
+    shares one)."""
+    items = [(np.asarray(ops[i]), list(ops[i + 1])) for i in range(0, len(ops), 2)]
+    if not items:
+        return np.ones(())
+    while len(items) > 1:
+        best = None
+        for i in range(len(items)):
+            for j in range(i + 1, len(items)):
+                (a, la), (b, lb) = items[i], items[j]
+                shared = [l for l in la if l in lb]
+                keep = [l for l in la if l not in shared] + [l for l in lb if l not in shared]
+                size = 1
+                for l in keep:
+                    size *= (a.shape[la.index(l)] if l in la else b.shape[lb.index(l)])
+                key = (0 if shared else 1, size, i, j)
+                if best is None or key < best[0]:
+                    best = (key, i, j, shared, keep)
+        _, i, j, shared, keep = best
+        (a, la), (b, lb) = items[i], items[j]
+        c = np.tensordot(a, b, axes=([la.index(l) for l in shared], [lb.index(l) for l in shared]))
+        items = [it for q, it in enumerate(items) if q not in (i, j)] + [(c, keep)]
+    y, ly = items[0]
+    extra = [l for l in ly if l not in out]
+    if extra:
+        raise ValueError("labels left uncontracted")
+    return np.transpose(y, [ly.index(l) for l in out]) if out else y
+
+
 def _block(k, pas, arrays, leaves, n_pos):
     """Y_k of the chain: the tensors at position k contracted together, an
     identity (delta) for every edge passing through, shaped (D_{k-1}, d_k, D_k)
@@ -499,37 +531,45 @@ def _block(k, pas, arrays, leaves, n_pos):
             ids[key] = len(ids)
         return ids[key]
 
-    ops = []
+    ops, core = [], []
     for t in pas["tensors"]:
         if phi[t] != k:
             continue
         sub = []
         for lab in legs[t]:
             if lab in lset:
-                sub.append(lid(("L", lab)))
+                key = ("L", lab)
             elif lab in rset:
-                sub.append(lid(("R", lab)))
+                key = ("R", lab)
             elif lab == leaf:
-                sub.append(lid(("X",)))
+                key = ("X",)
             else:
-                sub.append(lid(("I", lab)))
+                key = ("I", lab)
+            sub.append(lid(key))
+            if key[0] != "I":
+                core.append(key)
         ops += [arrays[t], sub]
+    # the tensors at k, summed over their internal edges
+    y = _contract_pairwise(ops, [ids[key] for key in core])
+    labels = list(core)
+    # a delta for every edge passing through, and for a leaf whose owner sits
+    # at another position
     for lab in left:
         if lab in rset:
-            ops += [np.eye(dim[lab]), [lid(("L", lab)), lid(("R", lab))]]
-    if leaf is not None and ("X",) not in ids:
+            y = np.multiply.outer(y, np.eye(dim[lab]))
+            labels += [("L", lab), ("R", lab)]
+    if leaf is not None and ("X",) not in labels:
         side = "L" if leaf in lset else "R"
-        ops += [np.eye(dim[leaf]), [lid((side, leaf)), lid(("X",))]]
-    out = [lid(("L", lab)) for lab in left]
+        y = np.multiply.outer(y, np.eye(dim[leaf]))
+        labels += [(side, leaf), ("X",)]
+    out = [("L", lab) for lab in left]
     if leaf is not None:
-        out.append(lid(("X",)))
-    out += [lid(("R", lab)) for lab in right]
+        out.append(("X",))
+    out += [("R", lab) for lab in right]
+    y = np.transpose(y, [labels.index(key) for key in out]) if out else y
     Dl = int(np.prod([dim[lab] for lab in left])) if left else 1
     Dr = int(np.prod([dim[lab] for lab in right])) if right else 1
     dk = dim[leaf] if leaf is not None else 1
-    if len(ids) > 52:
-        raise ValueError("block has too many labels for einsum")
-    y = np.einsum(*ops, out, optimize="greedy") if ops else np.ones(())
     return np.asarray(y, dtype=np.float64).reshape(Dl, dk, Dr)
 
 
