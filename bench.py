@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--batch", type=int, default=304)
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--value-path", type=int, default=1, choices=[0, 1],
+                   help="mixed-precision value path: 1 compensated FP32, 0 plain FFMA")
     p.add_argument("--no-fp64-arm", action="store_true",
                    help="skip the FP64-path measurement beside the headline (N=1 only)")
     p.add_argument("--no-batched-arm", action="store_true",
@@ -360,6 +362,7 @@ def bench_ours(args):
     ptrs = [sites.data_ptr() + 8 * elems * i for i in range(Bn)]
     plans = [plan] * Bn
     ctx = B.tn_ctx_create(local)
+    B.tn_ctx_set_option(ctx, B.TN_OPT_VALUE_PATH, args.value_path)
     stream = torch.cuda.current_stream(dev)
     sh = stream.cuda_stream
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2

@@ -47,22 +47,30 @@ typedef enum {
 
 /* Arithmetic of the hot path.
  *   TN_PREC_FP64:      every contraction, eigensolver and scale in FP64.
- *   TN_PREC_TF32:      FP32 storage; every contraction on tcgen05 tensor cores
- *                      as a compensated 3-term TF32 split (hi*hi + hi*lo +
- *                      lo*hi, FP32 accumulation, ~FP32 accuracy).  The density
- *                      matrix L_v = M_v R_v M_v^T is never formed: R_v = C_v
- *                      C_v^T (FP32 Cholesky), K_v = M_v C_v, and the leading
- *                      eigenvectors of L_v are the leading left singular
- *                      vectors of K_v (FP32 bidiagonal SVD), so L_v's spectrum
- *                      is resolved to ~eps_32^2 of its largest eigenvalue, as
- *                      an FP64 density matrix would be.  Root norm, log-scale
- *                      and the closing contraction in FP64.
+ *   TN_PREC_TF32:      FP32 storage.  The density-matrix side (memoised
+ *                      environments, K_v) on tcgen05 tensor cores as a
+ *                      compensated 3-term TF32 split (hi*hi + hi*lo + lo*hi,
+ *                      FP32 accumulation, ~FP32 accuracy); the value path
+ *                      (local blocks M_v, projections U_v^T M_v) in FP32 FFMA,
+ *                      whose rounding has no common sign (the tensor-core
+ *                      accumulator's does, and a bias of one sign in the tree
+ *                      tensors compounds over vertices and passes into ln Z).
+ *                      The density matrix L_v = M_v R_v M_v^T is never formed:
+ *                      R_v = C_v C_v^T (FP32 Cholesky with diagonal pivoting),
+ *                      K_v = M_v C_v, and the leading eigenvectors of L_v are
+ *                      the leading left singular vectors of K_v (FP32
+ *                      bidiagonal SVD), so L_v's spectrum is resolved to
+ *                      ~eps_32^2 of its largest eigenvalue, as an FP64
+ *                      density matrix would be.  A pass whose shapes exceed
+ *                      the factored kernels (dim A_v or a tree edge above
+ *                      128, a rank above 64) runs in the TN_PREC_TF32_GRAM
+ *                      form instead.  Root norm, log-scale and the closing
+ *                      contraction in FP64.
  *   TN_PREC_TF32_FAST: L_v formed explicitly in plain TF32 (memoised
- *                      environments too) and an FP32 eigensolver; only the
- *                      value path (local blocks, projections) is compensated.
- *                      Loses eigen-directions below ~1e-3 of the largest
- *                      eigenvalue.
- *   TN_PREC_TF32_GRAM: as TN_PREC_TF32_FAST with every contraction
+ *                      environments too) and an FP32 eigensolver; the value
+ *                      path as in TN_PREC_TF32.  Loses eigen-directions below
+ *                      ~1e-3 of the largest eigenvalue.
+ *   TN_PREC_TF32_GRAM: as TN_PREC_TF32_FAST with the density side
  *                      compensated: L_v in FP32 resolves eigen-directions only
  *                      down to ~1e-7 of its largest eigenvalue.
  *   TN_PREC_BF16:      reserved; returns TN_ERR_UNSUPPORTED in this build.  */
@@ -417,8 +425,13 @@ enum {
  *     a device flag that nothing sets.  The expired wait takes the kernel's
  *     error path (bounded drain of its copies in flight, tensor memory
  *     released) and the batch reports TN_ERR_TIMEOUT from tn_logz; the ctx
- *     stays usable.  It exercises the timeout handling without a fault.   */
-enum { TN_OPT_EIG_ROUNDS = 1, TN_OPT_WAIT_PROBE = 2 };
+ *     stays usable.  It exercises the timeout handling without a fault.
+ *   TN_OPT_VALUE_PATH: accumulation of the mixed-precision value path
+ *     (M_v = P_{v-1} Y_v, P_v = U_v^T M_v): 1 (default) compensated FP32
+ *     (Kahan, about FP64-accumulation accuracy), 0 plain FP32 FFMA (faster;
+ *     its rounding, amplified through the chain of projections, leaves
+ *     ~1e-6 of ln Z on 3D lattices).                                       */
+enum { TN_OPT_EIG_ROUNDS = 1, TN_OPT_WAIT_PROBE = 2, TN_OPT_VALUE_PATH = 3 };
 tn_status tn_ctx_set_option(tn_ctx_t* ctx, int32_t option, int64_t value);
 
 /* Turn per-launch CUDA-event timing on (1) or off (0) for later batches of

@@ -392,7 +392,7 @@ def tn_ctx_profile(ctx):
     return {k: (int(cnt[i]), float(ms[i])) for i, k in enumerate(KERNEL_CLASSES)}
 
 
-TN_OPT_EIG_ROUNDS, TN_OPT_WAIT_PROBE = 1, 2
+TN_OPT_EIG_ROUNDS, TN_OPT_WAIT_PROBE, TN_OPT_VALUE_PATH = 1, 2, 3
 
 
 def tn_rank_judged(ctx, n_inst):

@@ -115,6 +115,7 @@ struct tn_ctx {
   int* poll_flag = nullptr; // a device flag that nothing sets (TN_OPT_WAIT_PROBE)
   // options (tn_ctx_set_option)
   int eig_rounds = 9;       // SVD multisection rounds after the grid round
+  bool value_comp = true;   // compensated accumulation on the value path
   bool wait_probe = false;  // next batch: bounded wait on poll_flag in the GEMMs
   // result slot of each instance of the last batch (bucketed batches)
   std::vector<int> slot;
@@ -689,10 +690,11 @@ void run_plan(tn_ctx* c, const Bucket& bk, int precision, bool learned, cudaStre
 }
 
 // ------------------------------------------------------ mixed precision path
-// FP32 storage; density-matrix contractions (env, L_v) as TF32 tensor-core
-// products with FP32 accumulation; the value path (M_v, P_v) with the
-// compensated 3-term TF32 split; FP32 eigensolver; root norm, log-scale and
-// closing contraction accumulated in FP64.
+// FP32 storage; density-matrix contractions (env, K_v or L_v) as TF32
+// tensor-core products with FP32 accumulation (compensated 3-term split
+// except in the fast mode); the value path (M_v, P_v) in FP32 FFMA, whose
+// rounding has no common sign (the tensor-core accumulator's does); FP32
+// eigensolver or SVD; root norm, log-scale and closing contraction in FP64.
 struct WsF {
   long long sS, sY, sR, sX, sM, sL, sP, sUt, sLam, sAmax, sInv, sScr;
   float *S0, *S1, *Y, *Yt, *R, *X, *M, *Mt, *G, *L, *P, *Ut;
@@ -776,6 +778,11 @@ void tgemm(tn_ctx* c, int cls, const float* A, long long sA, int lda, const floa
   const bool aligned = (lda % 4 == 0) && (ldb % 4 == 0) && (sA % 4 == 0) && (sB % 4 == 0) &&
                        (reinterpret_cast<uintptr_t>(A) % 16 == 0) &&
                        (reinterpret_cast<uintptr_t>(Bm) % 16 == 0);
+  if (split == 2) {
+    // value path: FP32 FFMA, rounding to nearest at every step
+    ck(tn::launch_sgemm_ffma(g, c->value_comp, st), "ffma gemm launch");
+    return;
+  }
   if (aligned && c->tc_ready) {
     const std::array<int, 5> key{M, N, K, split, batch};
     if (c->tuning) {
@@ -866,9 +873,9 @@ void dm_pass_tc(tn_ctx* c, const tn::Step& st, const Lay& l, const WsF& w, float
     const int A = rp * dk;
     const float* Pp = (k == 1) ? w.Y + l.y_off[0] : w.P;
     const long long sPp = (k == 1) ? w.sY : w.sP;
-    // M_v = P_{v-1} Y_v (value path, compensated); also M_v^T for the projector.
+    // M_v = P_{v-1} Y_v (value path, FP32 FFMA); also M_v^T for the projector.
     tgemm(c, TN_KC_LOCAL, Pp, sPp, Dl, w.Yt + l.y_off[k], w.sY, Dl, w.M, w.sM, dk * Dr, w.Mt,
-          w.sM, A, Dr, rp, dk * Dr, Dl, B, nullptr, 0, nullptr, 0, 1, strm);
+          w.sM, A, Dr, rp, dk * Dr, Dl, B, nullptr, 0, nullptr, 0, 2, strm);
     float* Uk = Snext + l.s_off[k];
     if (factored) {
       // K_v = M_v C_k (C_k^T stored row-major: the K-major second operand)
@@ -891,15 +898,24 @@ void dm_pass_tc(tn_ctx* c, const tn::Step& st, const Lay& l, const WsF& w, float
          "eigh launch");
     }
     rank_hook<float>(c, pc, st, k, A, rk, w.lam, w.sLam, Uk, w.sS, w.Ut, w.sUt, B, strm);
-    // P_v = U_v^T M_v (value path, compensated)
+    // P_v = U_v^T M_v (value path, FP32 FFMA)
     tgemm(c, TN_KC_PROJECT, w.Ut, w.sUt, A, w.Mt, w.sM, A, w.P, w.sP, Dr, nullptr, 0, 0, 0, rk,
-          Dr, A, B, nullptr, 0, nullptr, 0, 1, strm);
+          Dr, A, B, nullptr, 0, nullptr, 0, 2, strm);
   }
   Scope(c, TN_KC_ROOT, strm),
   ck(tn::launch_root_f32(w.P, w.sP, D[n - 2], w.Y + l.y_off[n - 1], w.sY, st.r[n - 2], D[n - 2],
                          d[n - 1], Snext + l.s_off[n - 1], Snext + l.s_off[0], d[0], w.sS,
                          c->logscale, c->status, B, strm),
      "root launch");
+}
+
+// The factored form fits a pass when every vertex has dim A_v <= 128, tree
+// edge <= 128 and rank <= 64 (the register-resident Cholesky and SVD);
+// TN_PREC_TF32 runs the other passes in the compensated Gram form.
+bool factored_fits(const tn::Step& st) {
+  for (int k = 1; k <= st.n - 2; ++k)
+    if (!tn::svd_left_supported(st.r[k - 1] * st.d[k], st.D[k], st.r[k])) return false;
+  return true;
 }
 
 // Mixed path of one bucket (tables in place, results at c->logz etc.).
@@ -927,7 +943,8 @@ void run_plan_tc(tn_ctx* c, const Bucket& bk, int sub_split, bool factored, bool
                                   w.sScr, w.Y, w.sY, st.kind == 1 ? w.Yt : nullptr, B, strm);
       if (st.kind == 1) {
         const PassCtx pc = learn_pass(ls, c, st);
-        dm_pass_tc(c, st, lay[s], w, Snext, B, sub_split, factored, &tabs[s], strm, &pc);
+        dm_pass_tc(c, st, lay[s], w, Snext, B, sub_split, factored && factored_fits(st),
+                   &tabs[s], strm, &pc);
         std::swap(Scur, Snext);
       } else {
         int maxD = 1;
@@ -966,7 +983,8 @@ void run_plan_tc(tn_ctx* c, const Bucket& bk, int sub_split, bool factored, bool
                              strm),
          "fuse");
       const PassCtx pc = learn_pass(ls, c, st);
-      dm_pass_tc(c, st, lay[s], w, Snext, B, sub_split, factored, &tabs[s], strm, &pc);
+      dm_pass_tc(c, st, lay[s], w, Snext, B, sub_split, factored && factored_fits(st),
+                   &tabs[s], strm, &pc);
       std::swap(Scur, Snext);
     } else {
       Scope(c, TN_KC_FUSE, strm),
@@ -1032,15 +1050,6 @@ void run_batch(tn_ctx* c, const tn_plan_t* const* plans, int n, const double* co
   }
   if (learned && bks.size() > 1)
     fail(TN_ERR_UNSUPPORTED, "learned ranks need one plan structure per batch");
-  if (factored)
-    for (const Bucket& bk : bks)
-      for (const tn::Step& st : bk.P->steps) {
-        if (st.kind != 1) continue;
-        for (int k = 1; k <= st.n - 2; ++k)
-          if (!tn::svd_left_supported(st.r[k - 1] * st.d[k], st.D[k], st.r[k]))
-            fail(TN_ERR_UNSUPPORTED,
-                 "TN_PREC_TF32 needs dim A_v <= 128, tree-edge dims <= 128 and ranks <= 64");
-      }
   size_t ws_max = 0, ws_sum = 0, tab_tot = 0, res = 0;
   std::vector<int> slot(n, 0);
   for (Bucket& bk : bks) {
@@ -2055,6 +2064,9 @@ extern "C" tn_status tn_ctx_set_option(tn_ctx_t* c, int32_t option, int64_t valu
       c->eig_rounds = int(value);
     } else if (option == TN_OPT_WAIT_PROBE) {
       c->wait_probe = value != 0;
+    } else if (option == TN_OPT_VALUE_PATH) {
+      if (value != 0 && value != 1) fail(TN_ERR_INVALID, "TN_OPT_VALUE_PATH must be 0 or 1");
+      c->value_comp = value != 0;
     } else {
       fail(TN_ERR_INVALID, "unknown option");
     }

@@ -55,6 +55,9 @@ struct TcGemmArgs {
 };
 cudaError_t tc_gemm_configure();
 cudaError_t launch_sgemm_nt(const TcGemmArgs& g, cudaStream_t st);
+// FP32 FFMA (round to nearest) tiled GEMM of the same form: the value path;
+// compensated: Kahan accumulation (about FP64-accumulation accuracy).
+cudaError_t launch_sgemm_ffma(const TcGemmArgs& g, bool compensated, cudaStream_t st);
 cudaError_t launch_tc_gemm(const TcGemmArgs& g, cudaStream_t st);
 size_t tc_gemm_smem_bytes(int BN, int split, int K, int* stages_out, int budget_kb = 104);
 

@@ -425,6 +425,117 @@ __global__ void __launch_bounds__(256) k_sgemm_nt(TcGemmArgs g) {
   }
 }
 
+// C_i = alpha_i A_i B_i^T in FP32 with FFMA accumulation (round to nearest
+// at every step, so the rounding errors have no common sign), for the value
+// path of the mixed precision: on this part the tcgen05 FP32 accumulator
+// drops low bits (a relative bias of about -1e-8 per accumulated MMA, growing
+// with K), and a bias of one sign in the tree tensors compounds over the
+// vertices of a pass and over passes into ln Z.  64 x 64 tile per block of
+// 256 threads (4 x 4 per thread), K in chunks of 16 staged transposed in
+// shared memory.
+// kComp: compensated (Kahan) accumulation, y = fma(a, b, -c) rounded once
+// per term and the running sum's rounding carried in c: the dot product is
+// then accurate to a few eps of sqrt(sum of squared terms), like an FP64
+// accumulation of the FP32 products, at four FP32 operations per term.
+constexpr int kSgT = 64, kSgK = 16;
+template <bool kComp>
+__global__ void __launch_bounds__(256) k_sgemm_ffma(TcGemmArgs g) {
+  __shared__ float As[kSgK][kSgT + 4];
+  __shared__ float Bs[kSgK][kSgT + 4];
+  __shared__ float red[8];
+  const int i = blockIdx.z;
+  const int m0 = blockIdx.y * kSgT, n0 = blockIdx.x * kSgT;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const float* A = g.A + (long long)i * g.sA;
+  const float* B = g.B + (long long)i * g.sB;
+  const bool vec = (g.lda % 4 == 0) && (g.ldb % 4 == 0) && (g.sA % 4 == 0) && (g.sB % 4 == 0) &&
+                   (reinterpret_cast<uintptr_t>(g.A) % 16 == 0) &&
+                   (reinterpret_cast<uintptr_t>(g.B) % 16 == 0);
+  const int lr = tid >> 2, lk = (tid & 3) * 4;  // loader: row, first k of its 4
+  float acc[4][4], cmp[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = cmp[u][v] = 0.f;
+  for (int k0 = 0; k0 < g.K; k0 += kSgK) {
+    float av[4], bv[4];
+    const int am = m0 + lr, bn = n0 + lr, kk = k0 + lk;
+    if (vec && kk + 3 < g.K) {
+      const float4 a4 = (am < g.M) ? *reinterpret_cast<const float4*>(A + (long long)am * g.lda + kk)
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 b4 = (bn < g.N) ? *reinterpret_cast<const float4*>(B + (long long)bn * g.ldb + kk)
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+      av[0] = a4.x; av[1] = a4.y; av[2] = a4.z; av[3] = a4.w;
+      bv[0] = b4.x; bv[1] = b4.y; bv[2] = b4.z; bv[3] = b4.w;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        av[q] = (am < g.M && kk + q < g.K) ? A[(long long)am * g.lda + kk + q] : 0.f;
+        bv[q] = (bn < g.N && kk + q < g.K) ? B[(long long)bn * g.ldb + kk + q] : 0.f;
+      }
+    }
+    __syncthreads();  // the previous chunk's reads are done
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      As[lk + q][lr] = av[q];
+      Bs[lk + q][lr] = bv[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kSgK; ++k) {
+      const float4 a = *reinterpret_cast<const float4*>(&As[k][4 * ty]);
+      const float4 b = *reinterpret_cast<const float4*>(&Bs[k][4 * tx]);
+      const float ar[4] = {a.x, a.y, a.z, a.w}, br[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          if (kComp) {
+            const float y = fmaf(ar[u], br[v], -cmp[u][v]);
+            const float t = acc[u][v] + y;
+            cmp[u][v] = (t - acc[u][v]) - y;
+            acc[u][v] = t;
+          } else {
+            acc[u][v] = fmaf(ar[u], br[v], acc[u][v]);
+          }
+        }
+    }
+  }
+  float alpha = 1.f;
+  if (g.amax_in) {
+    const float mx = __uint_as_float(g.amax_in[(long long)i * g.s_amax_in]);
+    alpha = (mx > 0.f) ? 1.f / mx : 1.f;
+  }
+  float lmax = 0.f;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int m = m0 + 4 * ty + u;
+    if (m >= g.M) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int n = n0 + 4 * tx + v;
+      if (n >= g.N) continue;
+      const float x = acc[u][v] * alpha;
+      if (g.C) g.C[(long long)i * g.sC + (long long)m * g.ldc + n] = x;
+      if (g.Ct) {
+        const int q = n / g.ct_cols, cc = n - q * g.ct_cols;
+        g.Ct[(long long)i * g.sCt + (long long)cc * g.ldct + (long long)m * (g.N / g.ct_cols) + q] = x;
+      }
+      lmax = fmaxf(lmax, isfinite(x) ? fabsf(x) : INFINITY);
+    }
+  }
+  if (g.amax_out) {
+    for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    if ((tid & 31) == 0) red[tid >> 5] = lmax;
+    __syncthreads();
+    if (tid == 0) {
+      float v = red[0];
+      for (int w = 1; w < 8; ++w) v = fmaxf(v, red[w]);
+      atomicMax(g.amax_out + (long long)i * g.s_amax_out, __float_as_uint(v));
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_sgemm_nt(const TcGemmArgs& g, cudaStream_t st) {
@@ -433,6 +544,15 @@ cudaError_t launch_sgemm_nt(const TcGemmArgs& g, cudaStream_t st) {
   const long long tot = (long long)g.M * g.N;
   dim3 grid(unsigned((tot + 255) / 256), 1, g.batch);
   k_sgemm_nt<<<grid, 256, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sgemm_ffma(const TcGemmArgs& g, bool compensated, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
+  if (g.Ct && (g.ct_cols <= 0 || g.N % g.ct_cols)) return cudaErrorInvalidValue;
+  dim3 grid(unsigned((g.N + kSgT - 1) / kSgT), unsigned((g.M + kSgT - 1) / kSgT), g.batch);
+  if (compensated) k_sgemm_ffma<true><<<grid, 256, 0, st>>>(g);
+  else k_sgemm_ffma<false><<<grid, 256, 0, st>>>(g);
   return cudaGetLastError();
 }
 

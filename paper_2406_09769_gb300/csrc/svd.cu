@@ -6,9 +6,14 @@
 // rounding (~6e-8 of the largest eigenvalue) drowns every eigen-direction
 // below that level, and a truncation that falls there picks a subspace that
 // does not belong to the stored state.  This file never forms L_v:
-//   1. k_chol_env: R_v = C_v C_v^T (FP32 Cholesky, one CTA per R_v, every
-//      R_v of a pass in one launch; a non-positive pivot gives a zero column,
-//      so rank-deficient environments need no shift);
+//   1. k_chol_env: R_v = C_v C_v^T (FP32 Cholesky with diagonal pivoting,
+//      one CTA per R_v, every R_v of a pass in one launch).  The largest
+//      remaining diagonal entry is eliminated first and rows are not swapped
+//      (C = P L in the original row order); the factorisation stops once the
+//      remaining diagonal is below eps^2 of the first pivot, so a
+//      rank-deficient environment needs no shift.  Without pivoting, a
+//      rounding-level pivot met before the end divides the rest of its
+//      column by its square root and corrupts every later column;
 //   2. K_v = M_v C_v on the tensor cores (compensated TF32, elsewhere);
 //   3. k_svd_left: the leading left singular vectors of K_v, which are the
 //      leading eigenvectors of L_v = K_v K_v^T, and sigma^2 as its
@@ -77,7 +82,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_chol_env(float* __restrict__ R,
                                                           const int32_t* __restrict__ D,
                                                           const unsigned int* __restrict__ amax,
                                                           long long s_amax, int k0, int nk) {
-  __shared__ __align__(16) float Xc[2][128];
+  __shared__ __align__(16) float Xc[128];
+  __shared__ float dg[128];
+  __shared__ int dn[128];
   const int b = blockIdx.x / nk;
   const int k = k0 + blockIdx.x % nk;
   const int n = D[k];
@@ -96,60 +103,89 @@ __global__ void __launch_bounds__(kThreads, 2) k_chol_env(float* __restrict__ R,
       t[ii][jj] = (i < n && c < n) ? (Rg[(long long)i * n + c] + Rg[(long long)c * n + i]) * sc
                                    : 0.f;
     }
-  if (tb == 0)
-#pragma unroll
-    for (int ii = 0; ii < 8; ++ii) Xc[0][r0 + ii] = t[ii][0];
+  if (tid < 128) dn[tid] = 0;
   __syncthreads();  // every load of R_k done before the first store of C^T
+  float first = 0.f;
   for (int j = 0; j < n; ++j) {
-    const float* xc = Xc[j & 1];
-    const float p = xc[j];
-    const bool ok = p > 0.f && isfinite(p);
-    const float ip = ok ? 1.f / p : 0.f;
-    const float rs = ok ? rsqrtf(p) : 0.f;
-    // row j of C^T: C[l][j] = a_lj / sqrt(p) below the diagonal, sqrt(p) on it
-    for (int l = tid; l < n; l += kThreads) {
-      float v = 0.f;
-      if (ok && l > j) v = xc[l] * rs;
-      else if (ok && l == j) v = p * rs;
-      Rg[(long long)j * n + l] = v;
-    }
-    if (ok && r0 + 7 > j && c0 + 7 > j) {
-      const float4 ra = *reinterpret_cast<const float4*>(xc + r0);
-      const float4 rb = *reinterpret_cast<const float4*>(xc + r0 + 4);
-      const float4 ca = *reinterpret_cast<const float4*>(xc + c0);
-      const float4 cb = *reinterpret_cast<const float4*>(xc + c0 + 4);
-      const float rv[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
-      const float cv[8] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
-      float cm[8];
-#pragma unroll
-      for (int jj = 0; jj < 8; ++jj) cm[jj] = (c0 + jj > j) ? cv[jj] * ip : 0.f;
+    // the diagonal of the trailing matrix, eliminated rows excluded
+    if (ta == tb)
 #pragma unroll
       for (int ii = 0; ii < 8; ++ii) {
-        const float ri = (r0 + ii > j) ? rv[ii] : 0.f;
-        const float2 nr = make_float2(-ri, -ri);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float2 x = __ffma2_rn(nr, make_float2(cm[2 * q], cm[2 * q + 1]),
-                                      make_float2(t[ii][2 * q], t[ii][2 * q + 1]));
-          t[ii][2 * q] = x.x;
-          t[ii][2 * q + 1] = x.y;
-        }
+        const int i = r0 + ii;
+        if (i < n) dg[i] = dn[i] ? -1.f : t[ii][ii];
       }
+    __syncthreads();
+    // pivot: the largest remaining diagonal entry (first index on ties),
+    // found by every warp
+    float pv = -1.f;
+    int pi = n;
+    for (int i = lane; i < n; i += 32) {
+      const float x = dg[i];
+      if (x > pv) { pv = x; pi = i; }
     }
-    const int cn = j + 1;
-    if (cn < n && tb == (cn >> 3)) {
-      float* xn = Xc[cn & 1];
-      switch (cn & 7) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ov = __shfl_xor_sync(0xffffffffu, pv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, pi, o);
+      if (ov > pv || (ov == pv && oi < pi)) { pv = ov; pi = oi; }
+    }
+    if (j == 0) first = pv;
+    // stop below eps^2 of the first pivot (or at a non-finite one): the
+    // rounding of R_k (eps of its largest entry) then bounds every later
+    // entry of C by O(sqrt(first pivot)).  Pivots between eps^2 and eps of
+    // the first still carry environment directions that the truncation
+    // needs; dropping them biases which subspace the next vertices keep.
+    const bool ok = isfinite(pv) && pv > FLT_EPSILON * FLT_EPSILON * first && pv > 0.f;
+    if (!ok) {
+      for (long long q = (long long)j * n + tid; q < (long long)n * n; q += kThreads) Rg[q] = 0.f;
+      break;
+    }
+    if (tb == (pi >> 3)) {
+      switch (pi & 7) {
 #define TN_CHOL_PUB(E) \
   case E: {            \
-    _Pragma("unroll") for (int ii = 0; ii < 8; ++ii) xn[r0 + ii] = t[ii][E]; \
+    _Pragma("unroll") for (int ii = 0; ii < 8; ++ii) Xc[r0 + ii] = t[ii][E]; \
   } break;
         TN_CHOL_PUB(0) TN_CHOL_PUB(1) TN_CHOL_PUB(2) TN_CHOL_PUB(3)
         TN_CHOL_PUB(4) TN_CHOL_PUB(5) TN_CHOL_PUB(6) TN_CHOL_PUB(7)
 #undef TN_CHOL_PUB
       }
     }
+    if (tid == 0) dn[pi] = 1;
     __syncthreads();
+    const float ip = 1.f / pv;
+    const float rs = rsqrtf(pv);
+    // column j of C (row j of C^T): a_lp / sqrt(a_pp) on the rows not yet
+    // eliminated, sqrt(a_pp) on the pivot row, 0 on eliminated rows (C = P L
+    // in the original row order; C C^T = R_k / amax all the same)
+    for (int l = tid; l < n; l += kThreads) {
+      float v = 0.f;
+      if (l == pi) v = pv * rs;
+      else if (!dn[l]) v = Xc[l] * rs;
+      Rg[(long long)j * n + l] = v;
+    }
+    // rank-1 update of the whole tile (eliminated rows and columns are never
+    // read again)
+    const float4 ra = *reinterpret_cast<const float4*>(Xc + r0);
+    const float4 rb = *reinterpret_cast<const float4*>(Xc + r0 + 4);
+    const float4 ca = *reinterpret_cast<const float4*>(Xc + c0);
+    const float4 cb = *reinterpret_cast<const float4*>(Xc + c0 + 4);
+    const float rv[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
+    const float cv[8] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+    float cm[8];
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) cm[jj] = cv[jj] * ip;
+#pragma unroll
+    for (int ii = 0; ii < 8; ++ii) {
+      const float2 nr = make_float2(-rv[ii], -rv[ii]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 x = __ffma2_rn(nr, make_float2(cm[2 * q], cm[2 * q + 1]),
+                                    make_float2(t[ii][2 * q], t[ii][2 * q + 1]));
+        t[ii][2 * q] = x.x;
+        t[ii][2 * q + 1] = x.y;
+      }
+    }
   }
 }
 
@@ -785,6 +821,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_svd_left(const float* __restric
 #pragma unroll
       for (int kk = 0; kk < kQ; ++kk) z[kk] = fmaf(-d, vk[kk], z[kk]);
     }
+    const unsigned qm = 0xFu << (threadIdx.x & 28);
+    {
+      // unit norm to FP32 rounding: the reflectors, applied in FP32, leave
+      // |u| = 1 + O(p eps) with a bias of one sign, which would compound over
+      // the vertices of a pass and over passes (each pass's network is the
+      // previous tree); the norm is summed in FP64
+      double s2 = 0.0;
+#pragma unroll
+      for (int kk = 0; kk < kQ; ++kk) s2 = fma(double(z[kk]), double(z[kk]), s2);
+      for (int o = 1; o <= 2; o <<= 1) s2 += __shfl_xor_sync(qm, s2, o);
+      const float iv = (s2 > 0.0) ? float(1.0 / sqrt(s2)) : 0.f;
+#pragma unroll
+      for (int kk = 0; kk < kQ; ++kk) z[kk] *= iv;
+    }
     float best = -1.f;
     int bi = kNmax;
 #pragma unroll
@@ -793,7 +843,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_svd_left(const float* __restric
       const float av = fabsf(z[kk]);
       if (row < m && (av > best || (av == best && row < bi))) { best = av; bi = row; }
     }
-    const unsigned qm = 0xFu << (threadIdx.x & 28);
     for (int o = 1; o <= 2; o <<= 1) {
       const float ob = __shfl_xor_sync(qm, best, o);
       const int oi = __shfl_xor_sync(qm, bi, o);

@@ -132,9 +132,11 @@ def test_plan_rejects_malformed_input():
     with pytest.raises(B.TNError) as e:
         B.tn_plan(w["n"], bad, dims, 4, env_size=5)
     assert e.value.status == 1                       # endpoint out of range
+    # parts that are not row paths: the general planner takes them
+    assert B.tn_plan_query(B.tn_plan(w["n"], w["edges"], dims, 4, env_size=4))["general"] == 1
     with pytest.raises(B.TNError) as e:
-        B.tn_plan(w["n"], w["edges"], dims, 4, env_size=4)
-    assert e.value.status == 8                       # parts are not row paths
+        B.tn_plan(w["n"], w["edges"], dims, 4, env_size=5, planner=2)
+    assert e.value.status == 1                       # unknown planner
     with pytest.raises(B.TNError) as e:
         B.tn_plan(w["n"], w["edges"], dims, 4, env_size=5, path=[0, 1, 1, 3])
     assert e.value.status == 1                       # path not a permutation

@@ -87,7 +87,8 @@ def test_rows_general_equals_boundary_plan(ctx):
     a, sa = _run(ctx, [w], [_plan(w, 9, 6, 0, planner=1)])
     b, sb = _run(ctx, [w], [_plan(w, 9, 6, 0, planner=0)])
     assert sa[0] == 0 and sb[0] == 0
-    assert abs(a[0] - b[0]) / abs(b[0]) < 1e-12
+    # same tree and ranks; only the rounding order of the blocks differs
+    assert abs(a[0] - b[0]) / abs(b[0]) < RTOL_FP64
 
 
 def test_heterogeneous_random_graph_batch(ctx):
@@ -103,11 +104,27 @@ def test_heterogeneous_random_graph_batch(ctx):
         assert abs(logz[i] - ref) / abs(ref) < RTOL_FP64
 
 
-@pytest.mark.parametrize("name,make,env,chi,swap", [CASES[0], CASES[2], CASES[6]],
-                         ids=[CASES[i][0] for i in (0, 2, 6)])
+TF32_CASES = [CASES[0], CASES[2], CASES[5], CASES[6]]
+
+
+@pytest.mark.parametrize("name,make,env,chi,swap", TF32_CASES, ids=[c[0] for c in TF32_CASES])
 def test_tf32_matches_oracle(ctx, name, make, env, chi, swap):
     w = make()
     ref = _oracle(w, env, chi, swap)
     logz, status = _run(ctx, [w], [_plan(w, env, chi, swap)], B.TN_PREC_TF32)
     assert status[0] == 0
     assert abs(logz[0] - ref) / abs(ref) < RTOL_TF32
+
+
+def test_tf32_passes_beyond_factored_shapes_run_in_gram_form(ctx):
+    """Passes with tree edges above 128 (4-regular graph, parts of 2) run in
+    the compensated Gram form; the result still matches the oracle to the
+    Gram form's resolution of L_v (eigen-directions down to ~1e-7)."""
+    name, make, env, chi, swap = CASES[4]
+    w = make()
+    plan = _plan(w, env, chi, swap)
+    assert B.tn_plan_query(plan)["max_bond"] > 128
+    ref = _oracle(w, env, chi, swap)
+    logz, status = _run(ctx, [w], [plan], B.TN_PREC_TF32)
+    assert status[0] == 0
+    assert abs(logz[0] - ref) / abs(ref) < 1e-5
