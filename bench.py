@@ -57,6 +57,8 @@ def parse():
                    help="mixed-precision value path: 1 compensated FP32, 0 plain FFMA")
     p.add_argument("--no-fp64-arm", action="store_true",
                    help="skip the FP64-path measurement beside the headline (N=1 only)")
+    p.add_argument("--no-general-arms", action="store_true",
+                   help="skip the cubic and random-regular workloads (N=1 only)")
     p.add_argument("--no-batched-arm", action="store_true",
                    help="skip the heterogeneous-batch measurement (N=1 only)")
     return p.parse_args()
@@ -175,10 +177,8 @@ def hetero_workload(n=256):
 def batched_arm(B, torch, local, stream, flush):
     """The heterogeneous batch through one tn_contract_approx (untuned and
     after tn_autotune) and through a captured CUDA graph, each timed over two
-    steps after one warm-up; parity: graph == eager bit for bit, and the
-    first twelve instances small enough for the oracle (L <= 16, chi <= 32)
-    against it."""
-    from oracle import dmtree
+    steps after one warm-up; parity: graph == eager bit for bit (the oracle
+    check of the small instances runs in the CPU leg)."""
     work = hetero_workload()
     cache = {}
     plans, bufs = [], []
@@ -219,8 +219,6 @@ def batched_arm(B, torch, local, stream, flush):
     v_graph, ms_graph = timed(lambda: g.launch(sh))
     lz_g, st_g = g.logz()
     small = [i for i, (L, chi, _) in enumerate(work) if L <= 16 and chi <= 32][:12]
-    errs = [abs(lz_g[i] - dmtree.partitioned_contract_rows(work[i][2], work[i][1])["logz"]) /
-            abs(lz_g[i]) for i in small]
     return {"workload": "256 open 2D Gaussian spin glasses, beta 0.5, L in {12..32}, "
                         "chi in {16, 32, 48, 64} per instance (seeded); stands in for the "
                         "random 3-regular graphs, which need the general planner",
@@ -233,8 +231,161 @@ def batched_arm(B, torch, local, stream, flush):
             "status_ok": int((st_g == 0).sum()),
             "graph_equals_eager": bool(np.array_equal(lz_g, lz_e)),
             "tuned_equals_untuned": bool(np.array_equal(lz_e, lz_e0)),
-            "oracle_instances": len(small),
-            "max_rel_logz_err_vs_oracle": float(max(errs)) if errs else None}
+            "_check": [(i, work[i][0], work[i][1], float(lz_g[i])) for i in small]}
+
+
+_HETERO_ORACLE_SNIPPET = r"""
+import json, sys
+sys.path.insert(0, {root!r})
+from oracle import dmtree
+from workloads import ising
+out = []
+for i, L, chi in {items!r}:
+    w = ising.lattice2d(L, L, 0.5, "gauss", seed=4 * 10**6 + i)
+    out.append(dmtree.partitioned_contract_rows(w, chi)["logz"])
+print(json.dumps(out))
+"""
+
+
+def hetero_oracle_check(hetero):
+    """CPU leg: the FP64 oracle on the small instances of the heterogeneous
+    batch (L <= 16, chi <= 32, at most twelve)."""
+    chk = hetero.pop("_check")
+    code = _HETERO_ORACLE_SNIPPET.format(root=ROOT, items=[(i, L, c) for i, L, c, _ in chk])
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
+    ref = json.loads(r.stdout.strip().splitlines()[-1])
+    errs = [abs(lz - o) / abs(o) for (_, _, _, lz), o in zip(chk, ref)]
+    hetero["oracle_instances"] = len(errs)
+    hetero["max_rel_logz_err_vs_oracle"] = float(max(errs)) if errs else None
+
+
+# ------------------------------------------------ general-planner workloads
+
+CUBIC_BETAS = (0.20, 0.2217, 0.25)
+CUBIC_RUNS = ((1, 32), (2, 32), (3, 16), (3, 32), (3, 64))  # (sites per part, chi)
+RRG_PARTS, RRG_SWAP, RRG_BATCH, RRG_FP64 = 3, 4, 32, 4
+
+
+def _timed_call(torch, stream, flush, fn):
+    """One warm-up call, then one call timed with CUDA events on the stream."""
+    fn()
+    torch.cuda.synchronize()
+    flush.zero_()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def general_arms(B, torch, local, stream, flush):
+    """Workloads of the general planner.
+
+    cubic: the open 6x6x6 Ising ferromagnet at beta in CUBIC_BETAS (one batch
+    of three instances sharing a plan), parts of k consecutive sites of a
+    z-fibre, chi per CUBIC_RUNS, FP64 and TF32.
+    rrg: the first RRG_BATCH instances of the batched random 3-regular
+    workload (n in [40, 200], J = +-1, beta 0.3, chi per instance in
+    {16, 32, 48, 64}), parts of RRG_PARTS vertices along the recursive-bisection
+    order, swap batch RRG_SWAP: TF32 eager and graph replay, FP64 on the first
+    RRG_FP64.  ln Z values are returned for the oracle check of the CPU leg."""
+    from workloads import ising
+    sh = stream.cuda_stream
+    ctx = B.tn_ctx_create(local.index if local.index is not None else 0)
+    cubic = []
+    ws = [ising.cubic(6, 6, 6, b) for b in CUBIC_BETAS]
+    for k, chi in CUBIC_RUNS:
+        plan = B.tn_plan(216, ws[0]["edges"], np.full(len(ws[0]["edges"]), 2), chi, env_size=k)
+        info = B.tn_plan_query(plan)
+        bufs = [torch.from_numpy(B.pack_sites(plan, w["tensors"])).to(local) for w in ws]
+        ptrs = [b.data_ptr() for b in bufs]
+        row = {"sites_per_part": k, "chi": chi, "dm_passes": info["n_dm_passes"],
+               "max_tree_edge": info["max_bond"]}
+        for prec, name in ((B.TN_PREC_FP64, "fp64"), (B.TN_PREC_TF32, "tf32")):
+            ms = _timed_call(torch, stream, flush,
+                             lambda: B.tn_contract_approx(ctx, [plan] * 3, ptrs, prec, 0, sh))
+            lz, st = B.tn_logz(ctx, 3, raise_on_error=False)
+            row[name] = {"ms": ms, "value": 3 / (ms / 1e3), "logz": [float(x) for x in lz],
+                         "status_ok": int((st == 0).sum())}
+        cubic.append(row)
+    rws = [ising.config4_instance(i) for i in range(RRG_BATCH)]
+    plans = [B.tn_plan(w["n"], w["edges"], np.full(len(w["edges"]), 2), w["chi"],
+                       env_size=RRG_PARTS, swap_batch=RRG_SWAP) for w in rws]
+    infos = [B.tn_plan_query(p) for p in plans]
+    bufs = [torch.from_numpy(B.pack_sites(p, w["tensors"])).to(local) for p, w in zip(plans, rws)]
+    ptrs = [b.data_ptr() for b in bufs]
+    ms_e = _timed_call(torch, stream, flush,
+                       lambda: B.tn_contract_approx(ctx, plans, ptrs, B.TN_PREC_TF32, 0, sh))
+    lz_e, st_e = B.tn_logz(ctx, len(plans), raise_on_error=False)
+    g = B.Graph(ctx, plans, ptrs, B.TN_PREC_TF32)
+    ms_g = _timed_call(torch, stream, flush, lambda: g.launch(sh))
+    lz_g, _ = g.logz()
+    nf = RRG_FP64
+    ms_64 = _timed_call(torch, stream, flush,
+                        lambda: B.tn_contract_approx(ctx, plans[:nf], ptrs[:nf], B.TN_PREC_FP64,
+                                                     0, sh))
+    lz_64, st_64 = B.tn_logz(ctx, nf, raise_on_error=False)
+    rrg = {"workload": f"first {RRG_BATCH} instances of the 256 random 3-regular graphs "
+                       "(n in [40, 200], J = +-1, beta 0.3, chi in {16, 32, 48, 64} per "
+                       f"instance, seeded); parts of {RRG_PARTS} vertices, swap batch {RRG_SWAP}",
+           "instances": len(plans), "dm_passes": int(sum(q["n_dm_passes"] for q in infos)),
+           "max_tree_edge": int(max(q["max_bond"] for q in infos)),
+           "tf32_eager": {"value": len(plans) / (ms_e / 1e3), "ms": ms_e},
+           "tf32_graph_replay": {"value": len(plans) / (ms_g / 1e3), "ms": ms_g},
+           "graph_equals_eager": bool(np.array_equal(lz_g, lz_e)),
+           "fp64": {"value": nf / (ms_64 / 1e3), "ms": ms_64, "instances": nf},
+           "status_ok": int((st_e == 0).sum()),
+           "unit": "contractions/s",
+           "_logz_tf32": [float(x) for x in lz_e], "_logz_fp64": [float(x) for x in lz_64]}
+    return {"cubic_6x6x6": cubic, "random_3_regular": rrg}
+
+
+_GENERAL_ORACLE_SNIPPET = r"""
+import json, sys
+sys.path.insert(0, {root!r})
+from oracle import general
+from workloads import ising
+out = {{"cubic": [], "rrg": []}}
+for k, chi in {cubic_runs!r}:
+    w = ising.cubic(6, 6, 6, 0.2217)
+    out["cubic"].append(general.partitioned_contract_graph(w, general.parts_from_env(216, k), chi)["logz"])
+for i in range({n_rrg}):
+    w = ising.config4_instance(i)
+    out["rrg"].append(general.partitioned_contract_graph(
+        w, general.parts_from_env(w["n"], {parts}), w["chi"], {swap})["logz"])
+print(json.dumps(out))
+"""
+
+
+def general_oracle_check(gen):
+    """CPU leg: the FP64 oracle on the middle beta of every cubic run and on the
+    instances of the random-regular arm that ran in FP64; relative ln Z errors
+    of both precisions are written into gen."""
+    cores = os.cpu_count() or 1
+    env = dict(os.environ)
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(cores)
+    code = _GENERAL_ORACLE_SNIPPET.format(root=ROOT, cubic_runs=CUBIC_RUNS, n_rrg=RRG_FP64,
+                                          parts=RRG_PARTS, swap=RRG_SWAP)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
+    ref = json.loads(r.stdout.strip().splitlines()[-1])
+    for row, lz in zip(gen["cubic_6x6x6"], ref["cubic"]):
+        for name in ("fp64", "tf32"):
+            row[name]["rel_logz_err_vs_oracle_beta_0.2217"] = abs(row[name]["logz"][1] - lz) / abs(lz)
+    rrg = gen["random_3_regular"]
+    lz = np.asarray(ref["rrg"])
+    n = len(lz)
+    rrg["oracle_instances"] = n
+    rrg["max_rel_logz_err_tf32_vs_oracle"] = float(
+        np.max(np.abs(np.asarray(rrg["_logz_tf32"][:n]) - lz) / np.abs(lz)))
+    rrg["max_rel_logz_err_fp64_vs_oracle"] = float(
+        np.max(np.abs(np.asarray(rrg["_logz_fp64"][:n]) - lz) / np.abs(lz)))
 
 
 def pack_all(B, plan, ws):
@@ -517,6 +668,9 @@ def bench_ours(args):
     hetero = None
     if world == 1 and not args.no_batched_arm:
         hetero = batched_arm(B, torch, dev, stream, flush)
+    gen = None
+    if world == 1 and not args.no_general_arms:
+        gen = general_arms(B, torch, dev, stream, flush)
 
     out = {
         "metric": "approx contractions/s", "value": value, "unit": "contractions/s",
@@ -533,6 +687,7 @@ def bench_ours(args):
         "status_ok": int((status == 0).sum()),
         "measured_peaks_tflops": {k: round(v, 2) for k, v in mp.items()},
         "latency_batch1": lat, "fp64_arm": fp64_arm, "batched_heterogeneous": hetero,
+        "general_planner": gen,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         d = run_oracle(0, args.size, args.chi, args.cpu_seconds)
@@ -556,6 +711,16 @@ def bench_ours(args):
             if fp64_arm is not None:
                 out["fp64_arm"]["max_rel_logz_err_vs_exact"] = float(
                     np.max(np.abs(lz64[:len(ex)] - ex) / np.abs(ex)))
+    if hetero is not None:
+        if rank == 0 and not args.no_cpu_baseline:
+            hetero_oracle_check(hetero)
+        hetero.pop("_check", None)
+    if gen is not None:
+        if rank == 0 and not args.no_cpu_baseline:
+            general_oracle_check(gen)
+        rr = gen["random_3_regular"]
+        rr.pop("_logz_tf32")
+        rr.pop("_logz_fp64")
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
