@@ -265,7 +265,7 @@ def hetero_oracle_check(hetero):
 
 CUBIC_BETAS = (0.20, 0.2217, 0.25)
 CUBIC_RUNS = ((1, 32), (2, 32), (3, 16), (3, 32), (3, 64))  # (sites per part, chi)
-RRG_PARTS, RRG_SWAP, RRG_BATCH, RRG_FP64 = 3, 4, 32, 4
+RRG_PARTS, RRG_SWAP, RRG_BATCH, RRG_FP64 = 3, 4, 256, 4
 
 
 def _timed_call(torch, stream, flush, fn):
@@ -288,10 +288,11 @@ def general_arms(B, torch, local, stream, flush):
     cubic: the open 6x6x6 Ising ferromagnet at beta in CUBIC_BETAS (one batch
     of three instances sharing a plan), parts of k consecutive sites of a
     z-fibre, chi per CUBIC_RUNS, FP64 and TF32.
-    rrg: the first RRG_BATCH instances of the batched random 3-regular
-    workload (n in [40, 200], J = +-1, beta 0.3, chi per instance in
-    {16, 32, 48, 64}), parts of RRG_PARTS vertices along the recursive-bisection
-    order, swap batch RRG_SWAP: TF32 eager and graph replay, FP64 on the first
+    rrg: the RRG_BATCH instances of the batched random 3-regular workload
+    (n in [40, 200], J = +-1, beta 0.3, chi per instance in {16, 32, 48, 64}),
+    parts of RRG_PARTS vertices along the recursive-bisection order, swap batch
+    RRG_SWAP, in one call: TF32 on the grouped executor (every operation one
+    launch over all instances) eager and as a captured graph, FP64 on the first
     RRG_FP64.  ln Z values are returned for the oracle check of the CPU leg."""
     from workloads import ising
     sh = stream.cuda_stream
@@ -318,8 +319,10 @@ def general_arms(B, torch, local, stream, flush):
     infos = [B.tn_plan_query(p) for p in plans]
     bufs = [torch.from_numpy(B.pack_sites(p, w["tensors"])).to(local) for p, w in zip(plans, rws)]
     ptrs = [b.data_ptr() for b in bufs]
+    B.tn_ctx_profile(ctx)  # reset the launch counters
     ms_e = _timed_call(torch, stream, flush,
                        lambda: B.tn_contract_approx(ctx, plans, ptrs, B.TN_PREC_TF32, 0, sh))
+    n_launch = sum(v[0] for v in B.tn_ctx_profile(ctx).values()) // 2
     lz_e, st_e = B.tn_logz(ctx, len(plans), raise_on_error=False)
     g = B.Graph(ctx, plans, ptrs, B.TN_PREC_TF32)
     ms_g = _timed_call(torch, stream, flush, lambda: g.launch(sh))
@@ -329,9 +332,12 @@ def general_arms(B, torch, local, stream, flush):
                         lambda: B.tn_contract_approx(ctx, plans[:nf], ptrs[:nf], B.TN_PREC_FP64,
                                                      0, sh))
     lz_64, st_64 = B.tn_logz(ctx, nf, raise_on_error=False)
-    rrg = {"workload": f"first {RRG_BATCH} instances of the 256 random 3-regular graphs "
+    rrg = {"workload": f"{RRG_BATCH} random 3-regular graphs "
                        "(n in [40, 200], J = +-1, beta 0.3, chi in {16, 32, 48, 64} per "
                        f"instance, seeded); parts of {RRG_PARTS} vertices, swap batch {RRG_SWAP}",
+           "executor": "grouped: the instances advance in lockstep, every operation one "
+                       "launch over all instances' problems",
+           "launches_per_batch": int(n_launch),
            "instances": len(plans), "dm_passes": int(sum(q["n_dm_passes"] for q in infos)),
            "max_tree_edge": int(max(q["max_bond"] for q in infos)),
            "tf32_eager": {"value": len(plans) / (ms_e / 1e3), "ms": ms_e},

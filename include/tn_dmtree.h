@@ -430,8 +430,15 @@ enum {
  *     (M_v = P_{v-1} Y_v, P_v = U_v^T M_v): 1 (default) compensated FP32
  *     (Kahan, about FP64-accumulation accuracy), 0 plain FP32 FFMA (faster;
  *     its rounding, amplified through the chain of projections, leaves
- *     ~1e-6 of ln Z on 3D lattices).                                       */
-enum { TN_OPT_EIG_ROUNDS = 1, TN_OPT_WAIT_PROBE = 2, TN_OPT_VALUE_PATH = 3 };
+ *     ~1e-6 of ln Z on 3D lattices).
+ *   TN_OPT_GROUPED: a mixed-precision batch of more than eight plan
+ *     structures, all from the general planner, runs grouped: every
+ *     operation is one launch over the problems of several buckets, each
+ *     with its own pointers and shape (FP32 FFMA contractions, factored SVD
+ *     or Gram form per pass); the buckets advance in lockstep (global
+ *     step, pass section, tree vertex).  1 (default): on; 0: one launch
+ *     sequence per bucket on a pool of streams.                             */
+enum { TN_OPT_EIG_ROUNDS = 1, TN_OPT_WAIT_PROBE = 2, TN_OPT_VALUE_PATH = 3, TN_OPT_GROUPED = 4 };
 tn_status tn_ctx_set_option(tn_ctx_t* ctx, int32_t option, int64_t value);
 
 /* Turn per-launch CUDA-event timing on (1) or off (0) for later batches of

@@ -392,7 +392,7 @@ def tn_ctx_profile(ctx):
     return {k: (int(cnt[i]), float(ms[i])) for i, k in enumerate(KERNEL_CLASSES)}
 
 
-TN_OPT_EIG_ROUNDS, TN_OPT_WAIT_PROBE, TN_OPT_VALUE_PATH = 1, 2, 3
+TN_OPT_EIG_ROUNDS, TN_OPT_WAIT_PROBE, TN_OPT_VALUE_PATH, TN_OPT_GROUPED = 1, 2, 3, 4
 
 
 def tn_rank_judged(ctx, n_inst):

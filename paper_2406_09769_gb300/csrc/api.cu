@@ -77,6 +77,8 @@ struct tn_ctx {
   bool pending = false;
   // workspace
   DevBuf arena, stage, tables, results;
+  DevBuf gdesc;             // descriptor tables of grouped batches
+  DevBuf gguard;            // range table of the grouped guard mode
   void* pinned = nullptr;
   size_t pinned_cap = 0;
   cudaEvent_t pinned_free = nullptr;
@@ -116,6 +118,7 @@ struct tn_ctx {
   // options (tn_ctx_set_option)
   int eig_rounds = 9;       // SVD multisection rounds after the grid round
   bool value_comp = true;   // compensated accumulation on the value path
+  bool grouped = true;      // mixed batches of many general plans run grouped
   bool wait_probe = false;  // next batch: bounded wait on poll_flag in the GEMMs
   // result slot of each instance of the last batch (bucketed batches)
   std::vector<int> slot;
@@ -1002,6 +1005,590 @@ void run_plan_tc(tn_ctx* c, const Bucket& bk, int sub_split, bool factored, bool
   }
 }
 
+// ------------------------------------------------------ grouped mixed path
+// A batch of general plans (random graphs: one bucket per instance) as one
+// launch sequence.  Every bucket's path is a list of operations (block
+// gathers level by level, environment GEMMs, Cholesky factors, per tree
+// vertex the local block, density, eigenvectors and projection, the root,
+// the closing contraction), each at a position (global step, pass section,
+// tree vertex); the lists are merged so that the operations at the same
+// position share one launch over the problems of all buckets that have one,
+// each problem with its own pointers and shape (descriptor tables built on
+// the host once per batch).  Contractions run in FP32 FFMA (value path with
+// Kahan accumulation as on the bucketed path); eigenvectors by the factored
+// SVD where the pass fits it, else the Gram form.
+struct GLaunch {
+  int kind;            // 0 gather, 1 env root, 2 gemm, 3 gemm (value path), 4 chol,
+                       // 5 svd, 6 eigh, 7 root, 8 close
+  int cls;             // kernel class (TN_KC_*) of the launch
+  size_t off;          // byte offset of the descriptors in the table
+  int count;
+  int64_t p0, p1, p2;  // launch extents (max elements / max M, N / max m, n, r);
+                       // close: bucket, step
+};
+
+struct GBuild {
+  std::vector<char> bytes;
+  std::vector<GLaunch> launches;
+};
+
+// One operation of one bucket: its problems' descriptors and extents.
+struct GOp1 {
+  int kind, cls;
+  int64_t p0, p1, p2;
+  size_t esz;         // bytes per descriptor
+  std::vector<char> d;
+  std::array<int, 4> key;  // position in the path: step, section, index, sub-step
+};
+
+template <class D>
+void push_op(std::vector<GOp1>& ops, std::array<int, 4> key, int kind, int cls,
+             const std::vector<D>& ds, int64_t p0, int64_t p1 = 0, int64_t p2 = 0) {
+  if (ds.empty()) return;
+  GOp1 o{kind, cls, p0, p1, p2, sizeof(D), {}, key};
+  o.d.resize(sizeof(D) * ds.size());
+  std::memcpy(o.d.data(), ds.data(), o.d.size());
+  ops.push_back(std::move(o));
+}
+
+bool grouped_eligible(const std::vector<Bucket>& bks) {
+  for (const Bucket& bk : bks)
+    for (const tn::Step& st : bk.P->steps) {
+      if (!st.general) return false;
+      if (st.kind == 1)
+        for (int k = 1; k <= st.n - 2; ++k)
+          if (st.r[k - 1] * st.d[k] > 128 || st.r[k] > 64) return false;
+    }
+  return true;
+}
+
+// The operation list of bucket b (see above); res_* are the batch's result
+// arrays (bucket b's instances at b.res_off ..).
+std::vector<GOp1> bucket_ops(const std::vector<Bucket>& bks, size_t b, const WsF& w,
+                             bool factored, double* res_logscale, int* res_status,
+                             const tn::GuardTab* guard) {
+  const Bucket& bk = bks[b];
+  const int B = int(bk.idx.size());
+  std::vector<GOp1> ops;
+  int cur = 0;  // which of S0 / S1 holds the current MPS
+  auto S_of = [&](int which) { return which ? w.S1 : w.S0; };
+  for (size_t s = 0; s < bk.P->steps.size(); ++s) {
+    const tn::Step& st = bk.P->steps[s];
+    const Lay& l = bk.lay[s];
+    const StepTables& t = bk.tabs[s];
+    // blocks: the gather programs, level by level
+    for (size_t j = 0; j + 1 < st.level_start.size(); ++j) {
+      const int a = st.level_start[j], e = st.level_start[j + 1];
+      int64_t ne = 0;
+      for (int q = a; q < e; ++q) ne += st.gop[q].n_elems;
+      if (std::getenv("TN_GROUPED_CHECK")) {
+        // every element an op of this level reads or writes lies in its buffer
+        const int32_t* code = st.gcode.data();
+        for (int q = a; q < e; ++q) {
+          const tn::GOpH& op = st.gop[q];
+          if (op.to_block ? l.y_off[op.pos] + op.n_elems > w.sY : op.dst_off + op.n_elems > w.sScr)
+            fail(TN_ERR_INVALID, "grouped check: gather output out of range");
+          for (int u = 0; u < op.nt; ++u) {
+            const tn::GTensorH& g = st.gten[op.t_first + u];
+            int64_t ext = 1;
+            for (int v = 0; v < g.nleg; ++v)
+              ext += int64_t(code[op.code_off + code[g.leg_off + 2 * v]] - 1) *
+                     code[g.leg_off + 2 * v + 1];
+            int64_t base, lim;
+            if (g.src == 0) { base = bk.P->site_off[g.id]; lim = bk.P->site_elems; }
+            else if (g.src == 1) { base = bk.lay[s - 1].s_off[g.id]; lim = w.sS; }
+            else { base = g.id; lim = w.sScr; }
+            if (base + ext > lim) fail(TN_ERR_INVALID, "grouped check: gather operand out of range");
+          }
+        }
+      }
+      std::vector<tn::GatherDesc> ds;
+      for (int i = 0; i < B; ++i) {
+        tn::GatherDesc d{};
+        d.ops = t.gop; d.ten = t.gten; d.code = t.gcode; d.pre = t.gpre;
+        d.raw = bk.sites[i];
+        d.inv = w.inv + i * w.sInv;
+        d.S = S_of(cur) + i * w.sS;
+        d.scr = w.scr + i * w.sScr;
+        d.Y = w.Y + i * w.sY;
+        d.Yt = st.kind == 1 ? w.Yt + i * w.sY : nullptr;
+        d.a = a; d.b = e;
+        d.guard = guard;
+        ds.push_back(d);
+      }
+      push_op(ops, {int(s), 0, int(j), 0}, 0, TN_KC_FUSE, ds, ne);
+    }
+    if (st.kind == 2) {  // the closing contraction
+      GOp1 o{8, TN_KC_CLOSE, int64_t(b), int64_t(s), 0, 0, {}, {int(s), 1, 0, 0}};
+      ops.push_back(std::move(o));
+      continue;
+    }
+    if (st.kind != 1) continue;
+    const int n = st.n;
+    // start of the pass: R_{n-1} = [1], amax
+    {
+      std::vector<tn::EnvRootDesc> ds;
+      for (int i = 0; i < B; ++i)
+        ds.push_back({w.R + i * w.sR + l.r_off[n - 1], w.amax + i * w.sAmax, n, 0, guard});
+      push_op(ops, {int(s), 2, 0, 0}, 1, TN_KC_ENV, ds, 0);
+    }
+    // memoised environments, tree vertex k = n - 1 .. 2
+    for (int k = n - 1; k >= 2; --k) {
+      const int Dl = st.D[k - 1], Dr = st.D[k], dk = st.d[k];
+      std::vector<tn::GemmDesc> dx, dr;
+      for (int i = 0; i < B; ++i) {
+        const float* Yk = w.Y + i * w.sY + l.y_off[k];
+        float* X = w.X + i * w.sX;
+        tn::GemmDesc x{};
+        x.A = Yk; x.lda = Dr; x.B = w.R + i * w.sR + l.r_off[k]; x.ldb = Dr;
+        x.C = X; x.ldc = Dr; x.M = Dl * dk; x.N = Dr; x.K = Dr; x.ct_cols = Dr;
+        x.amax_in = w.amax + i * w.sAmax + k;
+        x.guard = guard;
+        dx.push_back(x);
+        tn::GemmDesc y{};
+        y.A = X; y.lda = dk * Dr; y.B = Yk; y.ldb = dk * Dr;
+        y.C = w.R + i * w.sR + l.r_off[k - 1]; y.ldc = Dl; y.M = Dl; y.N = Dl; y.K = dk * Dr;
+        y.ct_cols = Dl; y.amax_out = w.amax + i * w.sAmax + (k - 1);
+        y.guard = guard;
+        dr.push_back(y);
+      }
+      push_op(ops, {int(s), 3, n - 1 - k, 0}, 2, TN_KC_ENV, dx, int64_t(Dl) * dk, Dr);
+      push_op(ops, {int(s), 3, n - 1 - k, 1}, 2, TN_KC_ENV, dr, Dl, Dl);
+    }
+    const bool fact = factored && factored_fits(st);
+    if (fact) {
+      std::vector<tn::CholDesc> ds;
+      for (int i = 0; i < B; ++i)
+        for (int k = 1; k <= n - 2; ++k)
+          ds.push_back({w.R + i * w.sR + l.r_off[k], w.amax + i * w.sAmax + k, st.D[k], 0, guard});
+      push_op(ops, {int(s), 4, 0, 0}, 4, TN_KC_FACTOR, ds, 0);
+    }
+    // post-order over tree vertices k = 1 .. n - 2
+    float* Snext = S_of(1 - cur);
+    for (int k = 1; k <= n - 2; ++k) {
+      const int rp = st.r[k - 1], rk = st.r[k], dk = st.d[k], Dl = st.D[k - 1], Dr = st.D[k];
+      const int A = rp * dk;
+      std::vector<tn::GemmDesc> dm_, dk_, dl_, dp_;
+      std::vector<tn::SvdDesc> dsv;
+      std::vector<tn::EighDesc> deg;
+      for (int i = 0; i < B; ++i) {
+        const float* Pp = (k == 1) ? w.Y + i * w.sY + l.y_off[0] : w.P + i * w.sP;
+        float* M = w.M + i * w.sM;
+        float* Mt = w.Mt + i * w.sM;
+        float* G = w.G + i * w.sM;
+        float* Ut = w.Ut + i * w.sUt;
+        float* Uk = Snext + i * w.sS + l.s_off[k];
+        tn::GemmDesc g{};
+        g.A = Pp; g.lda = Dl; g.B = w.Yt + i * w.sY + l.y_off[k]; g.ldb = Dl;
+        g.C = M; g.ldc = dk * Dr; g.Ct = Mt; g.ldct = A; g.ct_cols = Dr;
+        g.M = rp; g.N = dk * Dr; g.K = Dl;
+        g.guard = guard;
+        dm_.push_back(g);
+        tn::GemmDesc q{};
+        q.A = M; q.lda = Dr; q.B = w.R + i * w.sR + l.r_off[k]; q.ldb = Dr;
+        q.C = G; q.ldc = Dr; q.M = A; q.N = Dr; q.K = Dr; q.ct_cols = Dr;
+        if (!fact) q.amax_in = w.amax + i * w.sAmax + k;  // G = M R_k / amax
+        q.guard = guard;
+        dk_.push_back(q);
+        if (fact) {
+          dsv.push_back({G, Uk, Ut, w.lam + i * w.sLam, res_status + bk.res_off + i, A, Dr, rk, 0,
+                         guard});
+        } else {
+          float* L = w.L + i * w.sL;
+          tn::GemmDesc h{};
+          h.A = G; h.lda = Dr; h.B = M; h.ldb = Dr; h.C = L; h.ldc = A;
+          h.M = A; h.N = A; h.K = Dr; h.ct_cols = A;
+          h.guard = guard;
+          dl_.push_back(h);
+          deg.push_back({L, Uk, Ut, w.lam + i * w.sLam, res_status + bk.res_off + i, A, rk, 0, 0,
+                         guard});
+        }
+        tn::GemmDesc pq{};
+        pq.A = Ut; pq.lda = A; pq.B = Mt; pq.ldb = A; pq.C = w.P + i * w.sP; pq.ldc = Dr;
+        pq.M = rk; pq.N = Dr; pq.K = A; pq.ct_cols = Dr;
+        pq.guard = guard;
+        dp_.push_back(pq);
+      }
+      push_op(ops, {int(s), 5, k, 0}, 3, TN_KC_LOCAL, dm_, rp, int64_t(dk) * Dr);
+      push_op(ops, {int(s), 5, k, 1}, 2, TN_KC_DENSITY, dk_, A, Dr);
+      push_op(ops, {int(s), 5, k, 2}, 2, TN_KC_DENSITY, dl_, A, A);
+      push_op(ops, {int(s), 5, k, 3}, 5, TN_KC_EIG, dsv, A, Dr, rk);
+      push_op(ops, {int(s), 5, k, 4}, 6, TN_KC_EIG, deg, A, rk);
+      push_op(ops, {int(s), 5, k, 5}, 3, TN_KC_PROJECT, dp_, rk, Dr);
+    }
+    // root M_r = P_{n-2} Y_{n-1}, unit norm into the log-scale
+    {
+      std::vector<tn::RootDesc> ds;
+      for (int i = 0; i < B; ++i) {
+        tn::RootDesc d{};
+        d.P = w.P + i * w.sP; d.Y = w.Y + i * w.sY + l.y_off[n - 1];
+        d.S_root = Snext + i * w.sS + l.s_off[n - 1]; d.S_first = Snext + i * w.sS + l.s_off[0];
+        d.logscale = res_logscale + bk.res_off + i;
+        d.status = res_status + bk.res_off + i;
+        d.ldp = st.D[n - 2]; d.r = st.r[n - 2]; d.D = st.D[n - 2]; d.d = st.d[n - 1];
+        d.d0 = st.d[0];
+        d.guard = guard;
+        ds.push_back(d);
+      }
+      push_op(ops, {int(s), 6, 0, 0}, 7, TN_KC_ROOT, ds, int64_t(st.r[n - 2]) * st.d[n - 1]);
+    }
+    cur = 1 - cur;
+  }
+  return ops;
+}
+
+// Merges the buckets' operation lists into one launch list: the buckets
+// advance in lockstep through global step s, pass section and tree vertex,
+// and the operations at the same position share a launch.  (A list schedule
+// led by the bucket with the most estimated work left merged fewer
+// operations per launch and ran ~15% slower on the random-graph batch.)
+// Closing contractions run alone: their launch takes one bucket's tables.
+void merge_grouped(const std::vector<std::vector<GOp1>>& per, GBuild& gb) {
+  const size_t nb = per.size();
+  std::vector<size_t> h(nb, 0);
+  while (true) {
+    int lead = -1;
+    for (size_t b = 0; b < nb; ++b)
+      if (h[b] < per[b].size() &&
+          (lead < 0 || per[b][h[b]].key < per[size_t(lead)][h[size_t(lead)]].key))
+        lead = int(b);
+    if (lead < 0) break;
+    const GOp1& o = per[size_t(lead)][h[size_t(lead)]];
+    if (o.kind == 8) {
+      gb.launches.push_back({8, o.cls, 0, 1, o.p0, o.p1, 0});
+      ++h[size_t(lead)];
+      continue;
+    }
+    GLaunch L{o.kind, o.cls, (gb.bytes.size() + 255) & ~size_t(255), 0, 0, 0, 0};
+    gb.bytes.resize(L.off);
+    for (size_t b = 0; b < nb; ++b) {
+      if (h[b] >= per[b].size()) continue;
+      const GOp1& x = per[b][h[b]];
+      if (x.kind != o.kind || x.key != o.key) continue;
+      gb.bytes.insert(gb.bytes.end(), x.d.begin(), x.d.end());
+      L.count += int(x.d.size() / x.esz);
+      L.p0 = std::max(L.p0, x.p0);
+      L.p1 = std::max(L.p1, x.p1);
+      L.p2 = std::max(L.p2, x.p2);
+      ++h[b];
+    }
+    gb.launches.push_back(L);
+  }
+}
+
+// Builds the launch list of a grouped batch (see above).
+void build_grouped(tn_ctx* c, const std::vector<Bucket>& bks, const std::vector<WsF>& ws,
+                   bool factored, double* res_logscale, int* res_status, GBuild& gb,
+                   const tn::GuardTab* guard = nullptr) {
+  std::vector<std::vector<GOp1>> per;
+  for (size_t b = 0; b < bks.size(); ++b)
+    per.push_back(bucket_ops(bks, b, ws[b], factored, res_logscale, res_status, guard));
+  merge_grouped(per, gb);
+}
+
+// Host-side range check of a grouped launch list (TN_GROUPED_CHECK=1): every
+// workspace operand of every descriptor must lie inside its bucket's
+// workspace slice; the first violation is reported and nothing launches.
+void check_grouped(const std::vector<Bucket>& bks, const GBuild& gb) {
+  std::vector<std::pair<uintptr_t, uintptr_t>> sl;
+  for (const Bucket& bk : bks) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(bk.ws_at);
+    sl.push_back({a, a + bk.ws_bytes});
+  }
+  std::sort(sl.begin(), sl.end());
+  auto inside = [&](const void* p, long long elems, size_t esz) {
+    if (!p || elems <= 0) return true;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p), e = a + uintptr_t(elems) * esz;
+    auto it = std::upper_bound(sl.begin(), sl.end(), std::make_pair(a, ~uintptr_t(0)));
+    if (it == sl.begin()) return false;
+    --it;
+    return a >= it->first && e <= it->second;
+  };
+  auto bad = [&](const char* what, size_t li, int q) {
+    fail(TN_ERR_INVALID, std::string("grouped check: ") + what + " out of its slice, launch " +
+                             std::to_string(li) + " problem " + std::to_string(q));
+  };
+  for (size_t li = 0; li < gb.launches.size(); ++li) {
+    const GLaunch& g = gb.launches[li];
+    const char* d = gb.bytes.data() + g.off;
+    for (int q = 0; q < g.count && g.kind != 8; ++q) {
+      if (g.kind == 2 || g.kind == 3) {
+        const tn::GemmDesc x = reinterpret_cast<const tn::GemmDesc*>(d)[q];
+        if (x.M > g.p0 || x.N > g.p1) bad("gemm extent", li, q);
+        if (!inside(x.A, (long long)(x.M - 1) * x.lda + x.K, 4)) bad("gemm A", li, q);
+        if (!inside(x.B, (long long)(x.N - 1) * x.ldb + x.K, 4)) bad("gemm B", li, q);
+        if (!inside(x.C, (long long)(x.M - 1) * x.ldc + x.N, 4)) bad("gemm C", li, q);
+        if (x.Ct && !inside(x.Ct, (long long)(x.ct_cols - 1) * x.ldct + (long long)x.M *
+                                      (x.N / x.ct_cols), 4))
+          bad("gemm Ct", li, q);
+        if (x.lda < x.K || x.ldb < x.K || x.ldc < x.N) bad("gemm leading dim", li, q);
+      } else if (g.kind == 5) {
+        const tn::SvdDesc x = reinterpret_cast<const tn::SvdDesc*>(d)[q];
+        if (x.m > g.p0 || x.n > g.p1 || x.r > g.p2 || x.r > x.m || x.r > x.n) bad("svd extent", li, q);
+        if (!inside(x.K, (long long)x.m * x.n, 4)) bad("svd K", li, q);
+        if (!inside(x.U, (long long)x.m * x.r, 4)) bad("svd U", li, q);
+        if (!inside(x.Ut, (long long)x.m * x.r, 4)) bad("svd Ut", li, q);
+      } else if (g.kind == 6) {
+        const tn::EighDesc x = reinterpret_cast<const tn::EighDesc*>(d)[q];
+        if (x.n > g.p0 || x.r > g.p1) bad("eigh extent", li, q);
+        if (!inside(x.L, (long long)x.n * x.n, 4)) bad("eigh L", li, q);
+        if (!inside(x.U, (long long)x.n * x.r, 4)) bad("eigh U", li, q);
+        if (!inside(x.Ut, (long long)x.n * x.r, 4)) bad("eigh Ut", li, q);
+      } else if (g.kind == 4) {
+        const tn::CholDesc x = reinterpret_cast<const tn::CholDesc*>(d)[q];
+        if (!inside(x.R, (long long)x.n * x.n, 4) || x.n > 128) bad("chol R", li, q);
+        if (!inside(x.amax, 1, 4)) bad("chol amax", li, q);
+      } else if (g.kind == 7) {
+        const tn::RootDesc x = reinterpret_cast<const tn::RootDesc*>(d)[q];
+        if ((long long)x.r * x.d > g.p0) bad("root extent", li, q);
+        if (!inside(x.P, (long long)(x.r - 1) * x.ldp + x.D, 4)) bad("root P", li, q);
+        if (!inside(x.Y, (long long)x.D * x.d, 4)) bad("root Y", li, q);
+        if (!inside(x.S_root, (long long)x.r * x.d, 4)) bad("root S", li, q);
+        if (!inside(x.S_first, (long long)x.d0 * x.d0, 4)) bad("root S_first", li, q);
+      } else if (g.kind == 1) {
+        const tn::EnvRootDesc x = reinterpret_cast<const tn::EnvRootDesc*>(d)[q];
+        if (!inside(x.R, 1, 4) || !inside(x.amax, x.n, 4)) bad("env root", li, q);
+      } else if (g.kind == 0) {
+        const tn::GatherDesc x = reinterpret_cast<const tn::GatherDesc*>(d)[q];
+        if (!inside(x.Y, 1, 4) || !inside(x.scr, 1, 8) || !inside(x.inv, 1, 8)) bad("gather", li, q);
+      }
+    }
+  }
+}
+
+void run_grouped_tc(tn_ctx* c, const std::vector<Bucket>& bks, bool factored, bool upload,
+                    double* res_logz, double* res_logscale, int* res_status, cudaStream_t strm) {
+  std::vector<WsF> ws;
+  for (const Bucket& bk : bks)
+    ws.push_back(carve_f32(c, bk.P, bk.lay, int(bk.idx.size()), false, nullptr, bk.ws_at));
+  for (size_t b = 0; b < bks.size(); ++b) {
+    const Bucket& bk = bks[b];
+    Scope(c, TN_KC_NORM, strm),
+    ck(tn::launch_site_norm(bk.tens_table, bk.off_dev, bk.len_dev, bk.P->n_vertices,
+                            int(bk.idx.size()), ws[b].inv, res_logscale + bk.res_off,
+                            res_status + bk.res_off, strm),
+       "site norm");
+  }
+  // guard mode (TN_GROUPED_GUARD=1, a diagnostic): every kernel checks its
+  // global accesses against the batch's allocations, the host synchronises
+  // after each launch and reports the first access outside them
+  const char* genv = std::getenv("TN_GROUPED_GUARD");
+  const bool guard_mode = genv && genv[0] == '1';
+  tn::GuardTab* gdev = nullptr;
+  unsigned long long* grec = nullptr;
+  struct Rg {
+    unsigned long long lo, hi;
+    std::string what;
+  };
+  std::vector<Rg> labelled;
+  if (guard_mode) {
+    auto addr = [](const void* q) { return (unsigned long long)reinterpret_cast<uintptr_t>(q); };
+    for (size_t b = 0; b < bks.size(); ++b) {
+      const Bucket& bk = bks[b];
+      labelled.push_back({addr(bk.ws_at), addr(bk.ws_at) + bk.ws_bytes,
+                          "workspace of bucket " + std::to_string(b)});
+      for (size_t i = 0; i < bk.sites.size(); ++i)
+        labelled.push_back({addr(bk.sites[i]),
+                            addr(bk.sites[i]) + sizeof(double) * size_t(bk.P->site_elems),
+                            "sites of bucket " + std::to_string(b) + " instance " +
+                                std::to_string(i)});
+    }
+    labelled.push_back({addr(c->tables.p), addr(c->tables.p) + c->tables.cap, "tables"});
+    labelled.push_back({addr(c->results.p), addr(c->results.p) + c->results.cap, "results"});
+    std::vector<std::pair<unsigned long long, unsigned long long>> rg;
+    for (const Rg& r : labelled) rg.push_back({r.lo, r.hi});
+    std::sort(rg.begin(), rg.end());
+    std::vector<std::pair<unsigned long long, unsigned long long>> mg;
+    for (const auto& r : rg) {
+      if (!mg.empty() && r.first <= mg.back().second) mg.back().second = std::max(mg.back().second, r.second);
+      else mg.push_back(r);
+    }
+    const int nr = int(mg.size());
+    const size_t head = 256, recb = 4 * sizeof(unsigned long long);
+    const size_t gbytes = head + recb + 2 * sizeof(unsigned long long) * size_t(nr);
+    char* gbase = static_cast<char*>(c->gguard.get(gbytes));
+    std::vector<char> img(gbytes, 0);
+    tn::GuardTab t{};
+    t.rec = reinterpret_cast<unsigned long long*>(gbase + head);
+    t.lo = reinterpret_cast<unsigned long long*>(gbase + head + recb);
+    t.hi = t.lo + nr;
+    t.n = nr;
+    std::memcpy(img.data(), &t, sizeof(t));
+    for (int i = 0; i < nr; ++i) {
+      std::memcpy(img.data() + head + recb + sizeof(unsigned long long) * i, &mg[i].first, 8);
+      std::memcpy(img.data() + head + recb + sizeof(unsigned long long) * (nr + i), &mg[i].second, 8);
+    }
+    ck(cudaStreamSynchronize(strm), "guard: sync");
+    ck(cudaMemcpy(gbase, img.data(), gbytes, cudaMemcpyHostToDevice), "guard: upload ranges");
+    gdev = reinterpret_cast<tn::GuardTab*>(gbase);
+    grec = t.rec;
+  }
+  GBuild gb;
+  build_grouped(c, bks, ws, factored, res_logscale, res_status, gb, gdev);
+  if (const char* e = std::getenv("TN_GROUPED_CHECK"))
+    if (e[0] == '1') {
+      check_grouped(bks, gb);
+      std::string st;
+      for (int kd = 0; kd <= 8; ++kd) {
+        long long n = 0, mc = 0, m0 = 0, m1 = 0, m2 = 0;
+        for (const GLaunch& g : gb.launches)
+          if (g.kind == kd) {
+            ++n; mc = std::max<long long>(mc, g.count); m0 = std::max<long long>(m0, g.p0);
+            m1 = std::max<long long>(m1, g.p1); m2 = std::max<long long>(m2, g.p2);
+          }
+        st += " k" + std::to_string(kd) + ":" + std::to_string(n) + "/" + std::to_string(mc) +
+              "/" + std::to_string(m0) + "," + std::to_string(m1) + "," + std::to_string(m2);
+      }
+      fail(TN_ERR_INVALID, "grouped check passed (" + std::to_string(gb.launches.size()) +
+                               " launches, " + std::to_string(gb.bytes.size()) + " bytes;" +
+                               st + "); nothing launched");
+    }
+  char* dbase = static_cast<char*>(c->gdesc.get(std::max<size_t>(gb.bytes.size(), 256)));
+  if (upload && !gb.bytes.empty())
+    ck(cudaMemcpyAsync(dbase, gb.bytes.data(), gb.bytes.size(), cudaMemcpyHostToDevice, strm),
+       "upload grouped tables");
+  if (guard_mode && !gb.bytes.empty()) {
+    std::vector<char> back(gb.bytes.size());
+    ck(cudaStreamSynchronize(strm), "guard: sync");
+    ck(cudaMemcpy(back.data(), dbase, back.size(), cudaMemcpyDeviceToHost), "guard: read back");
+    if (std::memcmp(back.data(), gb.bytes.data(), back.size()) != 0)
+      fail(TN_ERR_INVALID, "guard: device descriptor tables differ from the host image");
+  }
+  if (guard_mode && !gb.bytes.empty()) {
+    // the descriptor tables lie outside every allowed range
+    const unsigned long long d0 = (unsigned long long)reinterpret_cast<uintptr_t>(dbase);
+    const unsigned long long d1 = d0 + gb.bytes.size();
+    for (const Rg& r : labelled)
+      if (r.lo < d1 && d0 < r.hi)
+        fail(TN_ERR_INVALID, "guard: descriptor tables overlap " + r.what);
+  }
+  auto where = [&](unsigned long long a) {
+    const Rg* best = nullptr;
+    for (const Rg& r : labelled)
+      if (r.lo <= a && (!best || r.lo > best->lo)) best = &r;
+    if (!best) return std::string("below every allocation");
+    return best->what + " +" + std::to_string(a - best->lo) + " (size " +
+           std::to_string(best->hi - best->lo) + ")";
+  };
+  auto launch_bytes = [&](const GLaunch& g) -> size_t {
+    switch (g.kind) {
+      case 0: return sizeof(tn::GatherDesc) * size_t(g.count);
+      case 1: return sizeof(tn::EnvRootDesc) * size_t(g.count);
+      case 2: case 3: return sizeof(tn::GemmDesc) * size_t(g.count);
+      case 4: return sizeof(tn::CholDesc) * size_t(g.count);
+      case 5: return sizeof(tn::SvdDesc) * size_t(g.count);
+      case 6: return sizeof(tn::EighDesc) * size_t(g.count);
+      case 7: return sizeof(tn::RootDesc) * size_t(g.count);
+      default: return 0;
+    }
+  };
+  for (size_t li = 0; li < gb.launches.size(); ++li) {
+    const GLaunch& g = gb.launches[li];
+    char* d = dbase + g.off;
+    if (guard_mode && launch_bytes(g)) {
+      // this launch's descriptors are still as uploaded
+      std::vector<char> back(launch_bytes(g));
+      ck(cudaMemcpy(back.data(), d, back.size(), cudaMemcpyDeviceToHost), "guard: read back");
+      for (size_t q = 0; q < back.size(); ++q)
+        if (back[q] != gb.bytes[g.off + q])
+          fail(TN_ERR_INVALID, "guard: descriptors of launch " + std::to_string(li) + " kind " +
+                                   std::to_string(g.kind) + " changed on the device at byte " +
+                                   std::to_string(q) + " of " + std::to_string(back.size()) +
+                                   " (table offset " + std::to_string(g.off) + ")");
+    }
+    switch (g.kind) {
+      case 0:
+        Scope(c, g.cls, strm),
+        ck(tn::launch_gather_grouped(reinterpret_cast<tn::GatherDesc*>(d), g.count, g.p0, strm),
+           "grouped gather");
+        break;
+      case 1:
+        Scope(c, g.cls, strm),
+        ck(tn::launch_env_root_grouped(reinterpret_cast<tn::EnvRootDesc*>(d), g.count, strm),
+           "grouped env root");
+        break;
+      case 2:
+      case 3:
+        Scope(c, g.cls, strm),
+        ck(tn::launch_gemm_grouped(reinterpret_cast<tn::GemmDesc*>(d), g.count, int(g.p0),
+                                   int(g.p1), g.kind == 3 && c->value_comp, strm),
+           "grouped gemm");
+        break;
+      case 4:
+        Scope(c, g.cls, strm),
+        ck(tn::launch_chol_grouped(reinterpret_cast<tn::CholDesc*>(d), g.count, strm),
+           "grouped cholesky");
+        break;
+      case 5:
+        Scope(c, g.cls, strm),
+        ck(tn::launch_svd_left_grouped(reinterpret_cast<tn::SvdDesc*>(d), g.count, int(g.p0),
+                                       int(g.p1), int(g.p2), strm, c->eig_rounds),
+           "grouped svd");
+        break;
+      case 6:
+        Scope(c, g.cls, strm),
+        ck(tn::launch_eigh_grouped(reinterpret_cast<tn::EighDesc*>(d), g.count, int(g.p0),
+                                   int(g.p1), strm),
+           "grouped eigh");
+        break;
+      case 7:
+        Scope(c, g.cls, strm),
+        ck(tn::launch_root_grouped(reinterpret_cast<tn::RootDesc*>(d), g.count, int(g.p0), strm),
+           "grouped root");
+        break;
+      case 8: {
+        const Bucket& bk = bks[size_t(g.p0)];
+        const tn::Step& st = bk.P->steps[size_t(g.p1)];
+        int maxD = 1;
+        for (int k = 0; k < st.n; ++k) maxD = std::max(maxD, st.D[k]);
+        Scope(c, TN_KC_CLOSE, strm),
+        ck(tn::launch_close_f32(ws[size_t(g.p0)].Y, ws[size_t(g.p0)].sY,
+                                bk.tabs[size_t(g.p1)].y_off, bk.tabs[size_t(g.p1)].D, st.n, maxD,
+                                res_logscale + bk.res_off, res_logz + bk.res_off,
+                                res_status + bk.res_off, int(bk.idx.size()), strm),
+           "close");
+        break;
+      }
+      default:
+        fail(TN_ERR_INVALID, "grouped launch kind");
+    }
+    if (guard_mode) {
+      const std::string at = "guard: launch " + std::to_string(li) + " of " +
+                             std::to_string(gb.launches.size()) + " kind " +
+                             std::to_string(g.kind) + " count " + std::to_string(g.count) +
+                             " extents " + std::to_string(g.p0) + "," + std::to_string(g.p1) +
+                             "," + std::to_string(g.p2);
+      const cudaError_t e = cudaStreamSynchronize(strm);
+      if (e != cudaSuccess) fail(TN_ERR_CUDA, at + ": " + cudaGetErrorString(e));
+      unsigned long long rec[4] = {0, 0, 0, 0};
+      ck(cudaMemcpy(rec, grec, sizeof(rec), cudaMemcpyDeviceToHost), "guard: read record");
+      if (rec[0]) {
+        char tag[32];
+        std::snprintf(tag, sizeof(tag), "0x%llx", rec[0] - 1);
+        std::string m = at + ": access tag " + tag + " block " + std::to_string(rec[1]) +
+                        " value/address " + std::to_string(rec[2]) + " bytes/limit " +
+                        std::to_string(rec[3]) + " at " + where(rec[2]);
+        if (g.kind == 2 || g.kind == 3) {
+          const long long gx = (g.p1 + 63) / 64, gy = (g.p0 + 63) / 64;
+          const long long q = (long long)(rec[1] / (unsigned long long)(gx * gy));
+          if (q < g.count) {
+            const tn::GemmDesc x = reinterpret_cast<const tn::GemmDesc*>(gb.bytes.data() + g.off)[q];
+            auto ad = [](const void* v) { return (unsigned long long)reinterpret_cast<uintptr_t>(v); };
+            m += "; problem " + std::to_string(q) + " M " + std::to_string(x.M) + " N " +
+                 std::to_string(x.N) + " K " + std::to_string(x.K) + " lda " +
+                 std::to_string(x.lda) + " ldb " + std::to_string(x.ldb) + " ldc " +
+                 std::to_string(x.ldc) + " ldct " + std::to_string(x.ldct) + " ct_cols " +
+                 std::to_string(x.ct_cols) + " A at " + where(ad(x.A)) + " B at " +
+                 where(ad(x.B)) + " C at " + where(ad(x.C)) +
+                 (x.Ct ? " Ct at " + where(ad(x.Ct)) : std::string());
+          }
+        }
+        fail(TN_ERR_INVALID, m);
+      }
+    }
+  }
+}
+
 constexpr size_t kPoolStreams = 8;  // concurrent buckets of one batch
 
 // Restores the ctx's result pointers after a bucketed batch (also on error).
@@ -1110,14 +1697,20 @@ void run_batch(tn_ctx* c, const tn_plan_t* const* plans, int n, const double* co
     for (size_t i = 0; i < order.size(); ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(),
                      [&](size_t a, size_t b) { return bks[a].ws_bytes > bks[b].ws_bytes; });
-    for (size_t j = 0; j < order.size(); ++j) {
-      const Bucket& bk = bks[order[j]];
-      cudaStream_t bs = nstreams ? c->pool[j % nstreams] : strm;
-      view.at(bk.res_off);
-      if (tc)
-        run_plan_tc(c, bk, sub_split, factored, learned, bs);
-      else
-        run_plan(c, bk, precision, learned, bs);
+    const bool grouped = tc && c->grouped && !learned && bks.size() > kPoolStreams &&
+                         grouped_eligible(bks);
+    if (grouped) {
+      run_grouped_tc(c, bks, factored, upload, view.logz, view.logscale, view.status, strm);
+    } else {
+      for (size_t j = 0; j < order.size(); ++j) {
+        const Bucket& bk = bks[order[j]];
+        cudaStream_t bs = nstreams ? c->pool[j % nstreams] : strm;
+        view.at(bk.res_off);
+        if (tc)
+          run_plan_tc(c, bk, sub_split, factored, learned, bs);
+        else
+          run_plan(c, bk, precision, learned, bs);
+      }
     }
     if (nstreams)
       for (int q = 0; q < nstreams; ++q) {
@@ -1984,6 +2577,8 @@ extern "C" tn_status tn_batch_graph_capture(tn_ctx_t* c, const tn_plan_t* const*
       fail(TN_ERR_UNSUPPORTED, "tcgen05 path unavailable on this device");
     g->own->eig_rounds = c->eig_rounds;
     g->own->tune = c->tune;
+    g->own->grouped = c->grouped;
+    g->own->value_comp = c->value_comp;
     g->n = n_inst;
     ck(cudaDeviceSynchronize(), "cudaDeviceSynchronize");  // site buffers ready for cap
     ck(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "cudaStreamCreate");
@@ -2067,6 +2662,9 @@ extern "C" tn_status tn_ctx_set_option(tn_ctx_t* c, int32_t option, int64_t valu
     } else if (option == TN_OPT_VALUE_PATH) {
       if (value != 0 && value != 1) fail(TN_ERR_INVALID, "TN_OPT_VALUE_PATH must be 0 or 1");
       c->value_comp = value != 0;
+    } else if (option == TN_OPT_GROUPED) {
+      if (value != 0 && value != 1) fail(TN_ERR_INVALID, "TN_OPT_GROUPED must be 0 or 1");
+      c->grouped = value != 0;
     } else {
       fail(TN_ERR_INVALID, "unknown option");
     }

@@ -568,7 +568,8 @@ __device__ int sturm_count_fast(const T* dd, const T* e2, int n, T x, T pivmin) 
 // padded reflector rows R, then signs (largest-|.| entry, first on ties,
 // positive) and the stores U (n x r) and Ut (r x n).
 __device__ void vectors_f32(const float* Zs, int zld, const float* zscale, int n, int r,
-                            const float* R, const float* tau, float* pub, float* U, float* Ut) {
+                            const float* R, const float* tau, float* pub, float* U, float* Ut,
+                            const GuardTab* gd = nullptr) {
   const int tid = threadIdx.x, col = tid >> 2, qr = tid & 3;
   const bool live = col < r;
   const float zs = live ? zscale[col] : 0.f;
@@ -659,8 +660,10 @@ __device__ void vectors_f32(const float* Zs, int zld, const float* zscale, int n
     for (int kk = 0; kk < kQ; ++kk) {
       const int row = qr * kQ + kk;
       if (row < n) {
-        U[(long long)row * r + col] = sgn * z[kk];
-        if (Ut) Ut[(long long)col * n + row] = sgn * z[kk];
+        if (guard_ok(gd, U + (long long)row * r + col, 4, 0x607))
+          U[(long long)row * r + col] = sgn * z[kk];
+        if (Ut && guard_ok(gd, Ut + (long long)col * n + row, 4, 0x608))
+          Ut[(long long)col * n + row] = sgn * z[kk];
       }
     }
   }
@@ -676,14 +679,27 @@ __host__ __device__ __forceinline__ int fast_region_a(int n) {
   return m > rr ? m : rr;
 }
 
+// desc != NULL (FP32 only): grouped launch, CTA i solves problem desc[i].
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg, long long sL,
-                                                        T* __restrict__ Ug, long long sU,
-                                                        T* __restrict__ Utg, long long sUt,
-                                                        double* __restrict__ lamg, long long slam,
-                                                        int n, int r, int nlam, int* status) {
+__global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg_, long long sL,
+                                                        T* __restrict__ Ug_, long long sU,
+                                                        T* __restrict__ Utg_, long long sUt,
+                                                        double* __restrict__ lamg_, long long slam,
+                                                        int n_, int r_, int nlam_, int* status_,
+                                                        const EighDesc* __restrict__ desc) {
   extern __shared__ __align__(16) unsigned char raw[];
   __shared__ T scal[8];
+  // grouped launch: CTA i solves problem desc[i] with its own pointers and
+  // shape; else instance blockIdx.x of the strided arguments
+  const EighDesc* qd = desc ? desc + blockIdx.x : nullptr;
+  const GuardTab* gd = qd ? qd->guard : nullptr;
+  const int b = qd ? 0 : int(blockIdx.x);
+  const T* Lg = qd ? reinterpret_cast<const T*>(qd->L) : Lg_;
+  T* Ug = qd ? reinterpret_cast<T*>(qd->U) : Ug_;
+  T* Utg = qd ? reinterpret_cast<T*>(qd->Ut) : Utg_;
+  double* lamg = qd ? qd->lam : lamg_;
+  int* status = qd ? qd->status : status_;
+  const int n = qd ? qd->n : n_, r = qd ? qd->r : r_, nlam = qd ? qd->nlam : nlam_;
   const int ld = n + 1;
   const int nl = (nlam > r) ? nlam : r;
   // the 128-entry vectors first (16-byte aligned), then A and Z
@@ -700,7 +716,6 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
   T* A = shift + 64;                  // n x ld; FP32: reflector rows R overlay it
   T* Zs = A + fast_region_a<T>(n);    // r vectors of length n, padded to n + 1
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int b = blockIdx.x;
   const T* L = Lg + (long long)b * sL;
 
   // L copied row by row with coalesced loads, then symmetrised in place,
@@ -708,7 +723,10 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
   // forming each element from L directly; the column reads have pitch n + 1)
   bool bad = false;
   for (int a = warp; a < n; a += kThreads / 32)
-    for (int c = lane; c < n; c += 32) A[a * ld + c] = L[(long long)a * n + c];
+    for (int c = lane; c < n; c += 32)
+      A[a * ld + c] = guard_ok(gd, L + (long long)a * n + c, sizeof(T), 0x601)
+                          ? L[(long long)a * n + c]
+                          : T(0);
   __syncthreads();
   for (int a = warp; a < n; a += kThreads / 32)
     for (int c = a + lane; c < n; c += 32) {
@@ -718,10 +736,14 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
       A[c * ld + a] = x;
     }
   if (__syncthreads_or(bad)) {
-    for (int idx = tid; idx < n * r; idx += kThreads) Ug[(long long)b * sU + idx] = T(0);
+    for (int idx = tid; idx < n * r; idx += kThreads)
+      if (guard_ok(gd, Ug + (long long)b * sU + idx, sizeof(T), 0x602))
+        Ug[(long long)b * sU + idx] = T(0);
     if (Utg)
-      for (int idx = tid; idx < n * r; idx += kThreads) Utg[(long long)b * sUt + idx] = T(0);
-    if (tid == 0) status[b] = TN_ERR_NONFINITE;
+      for (int idx = tid; idx < n * r; idx += kThreads)
+        if (guard_ok(gd, Utg + (long long)b * sUt + idx, sizeof(T), 0x603))
+          Utg[(long long)b * sUt + idx] = T(0);
+    if (tid == 0 && guard_ok(gd, status + b, 4, 0x605)) status[b] = TN_ERR_NONFINITE;
     return;
   }
 
@@ -994,7 +1016,7 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
                 reinterpret_cast<const float*>(vscale), n, r,
                 reinterpret_cast<const float*>(A), reinterpret_cast<const float*>(tau),
                 reinterpret_cast<float*>(pub), reinterpret_cast<float*>(Ug) + (long long)b * sU,
-                Utg ? reinterpret_cast<float*>(Utg) + (long long)b * sUt : nullptr);
+                Utg ? reinterpret_cast<float*>(Utg) + (long long)b * sUt : nullptr, gd);
   } else {
   // ---- 4. vectors into registers: thread = (column c, quarter q of the rows)
   const int col = tid >> 2, qr = tid & 3;
@@ -1091,7 +1113,8 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
   }
   if (lamg) {
     double* lo = lamg + (long long)b * slam;
-    for (int t = tid; t < nlam && t < n; t += kThreads) lo[t] = double(lam[t]);
+    for (int t = tid; t < nlam && t < n; t += kThreads)
+      if (guard_ok(gd, lo + t, 8, 0x609)) lo[t] = double(lam[t]);
   }
 }
 
@@ -1117,7 +1140,7 @@ cudaError_t launch_eigh_top(const T* L, long long sL, T* U, long long sU, T* Ut,
   const size_t fast_smem = eigh_fast_smem_bytes<T>(n, r);
   if (r <= 64 && fast_smem <= eigh_fast_smem_limit<T>()) {
     k_eigh_fast<T><<<batch, kThreads, fast_smem, st>>>(L, sL, U, sU, Ut, sUt, lam, slam, n, r,
-                                                       nlam, status);
+                                                       nlam, status, nullptr);
     return cudaGetLastError();
   }
   const size_t smem = eigh_smem_bytes<T>(n, r, nlam);
@@ -1166,6 +1189,17 @@ cudaError_t eigh_configure() {
   if (e == cudaSuccess) e = configure_kernel(k_eigh_fast<double>, &g_limit[2]);
   if (e == cudaSuccess) e = configure_kernel(k_eigh_fast<float>, &g_limit[3]);
   return e;
+}
+
+cudaError_t launch_eigh_grouped(const EighDesc* desc, int n_prob, int max_n, int max_r,
+                                cudaStream_t st) {
+  if (n_prob <= 0) return cudaSuccess;
+  if (max_n < 1 || max_n > kNmax || max_r < 1 || max_r > 64) return cudaErrorInvalidValue;
+  const size_t smem = eigh_fast_smem_bytes<float>(max_n, max_r);
+  if (smem > eigh_fast_smem_limit<float>()) return cudaErrorInvalidValue;
+  k_eigh_fast<float><<<n_prob, kThreads, smem, st>>>(nullptr, 0, nullptr, 0, nullptr, 0, nullptr,
+                                                     0, 0, 0, 0, nullptr, desc);
+  return cudaGetLastError();
 }
 
 template size_t eigh_smem_bytes<double>(int, int, int);

@@ -163,6 +163,112 @@ cudaError_t launch_iota(int* x, int n, cudaStream_t st);
 // launch_svd_left: the r (<= 64) leading left singular vectors of K_i (m x n,
 // row-major, m, n <= 128) into U (m x r) and Ut (r x m, may be NULL), signed
 // so the largest-|.| entry is positive, and sigma_t^2 for t < nlam into lam.
+// ---- grouped launches: one launch over problems of different buckets (plans)
+// and shapes; every problem carries its own pointers.
+// Range guard (a diagnostic mode of the grouped executor): the sorted device
+// allocations [lo[i], hi[i]) every global access must fall in.  A kernel whose
+// descriptor carries a guard checks each global access before making it; the
+// first one outside every allocation is recorded in rec (tag + 1, linear
+// block index, address, bytes) and skipped.
+struct GuardTab {
+  const unsigned long long* lo;
+  const unsigned long long* hi;
+  unsigned long long* rec;
+  int n, pad;
+};
+#ifdef __CUDACC__
+__device__ __forceinline__ bool guard_ok(const GuardTab* g, const void* p, long long bytes,
+                                         int tag) {
+  if (!g) return true;
+  const unsigned long long a = reinterpret_cast<unsigned long long>(p);
+  int lo = 0, hi = g->n - 1, f = -1;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    if (g->lo[mid] <= a) {
+      f = mid;
+      lo = mid + 1;
+    } else {
+      hi = mid - 1;
+    }
+  }
+  if (f >= 0 && bytes >= 0 && a + (unsigned long long)bytes <= g->hi[f]) return true;
+  if (atomicCAS(g->rec, 0ull, (unsigned long long)tag + 1ull) == 0ull) {
+    g->rec[1] = blockIdx.x + (unsigned long long)gridDim.x *
+                                 (blockIdx.y + (unsigned long long)gridDim.y * blockIdx.z);
+    g->rec[2] = a;
+    g->rec[3] = (unsigned long long)bytes;
+  }
+  return false;
+}
+// A note of the guard mode: records (tag, block, v0, v1) if nothing was
+// recorded before.
+__device__ __forceinline__ void guard_note(const GuardTab* g, int tag, unsigned long long v0,
+                                           unsigned long long v1) {
+  if (!g) return;
+  if (atomicCAS(g->rec, 0ull, (unsigned long long)tag + 1ull) == 0ull) {
+    g->rec[1] = blockIdx.x + (unsigned long long)gridDim.x *
+                                 (blockIdx.y + (unsigned long long)gridDim.y * blockIdx.z);
+    g->rec[2] = v0;
+    g->rec[3] = v1;
+  }
+}
+// An index check of the guard mode: false (and recorded, value in place of
+// the address) unless 0 <= v < lim.
+__device__ __forceinline__ bool guard_idx(const GuardTab* g, long long v, long long lim, int tag) {
+  if (!g || (v >= 0 && v < lim)) return true;
+  if (atomicCAS(g->rec, 0ull, (unsigned long long)tag + 1ull) == 0ull) {
+    g->rec[1] = blockIdx.x + (unsigned long long)gridDim.x *
+                                 (blockIdx.y + (unsigned long long)gridDim.y * blockIdx.z);
+    g->rec[2] = (unsigned long long)v;
+    g->rec[3] = (unsigned long long)lim;
+  }
+  return false;
+}
+#endif
+struct SvdDesc {
+  const float* K; float* U; float* Ut; double* lam; int* status;
+  int m, n, r, nlam;
+  const GuardTab* guard;
+};
+struct CholDesc {
+  float* R; const unsigned int* amax; int n, pad;
+  const GuardTab* guard;
+};
+// C = alpha A B^T (A: M x K, B: N x K, K-major), alpha = 1 / *amax_in if set;
+// Ct (optional): columns grouped as in TcGemmArgs::ct_cols; max|C| folded
+// into *amax_out if set.
+struct GemmDesc {
+  const float* A; const float* B; float* C; float* Ct;
+  const unsigned int* amax_in; unsigned int* amax_out;
+  int M, N, K, lda, ldb, ldc, ldct, ct_cols;
+  const GuardTab* guard;
+};
+struct RootDesc {
+  const float* P; const float* Y; float* S_root; float* S_first;
+  double* logscale; int* status;
+  int ldp, r, D, d, d0, pad;
+  const GuardTab* guard;
+};
+// Start of a pass: amax[0 .. n-2] = 0, R_{n-1} = [1] at R, amax[n-1] = 1.
+struct EnvRootDesc {
+  float* R; unsigned int* amax; int n, pad;
+  const GuardTab* guard;
+};
+cudaError_t launch_svd_left_grouped(const SvdDesc* desc, int n_prob, int max_m, int max_n,
+                                    int max_r, cudaStream_t st, int rounds = 9);
+cudaError_t launch_chol_grouped(const CholDesc* desc, int n_prob, cudaStream_t st);
+cudaError_t launch_gemm_grouped(const GemmDesc* desc, int n_prob, int max_M, int max_N,
+                                bool compensated, cudaStream_t st);
+cudaError_t launch_root_grouped(const RootDesc* desc, int n_prob, int max_rd, cudaStream_t st);
+cudaError_t launch_env_root_grouped(const EnvRootDesc* desc, int n_prob, cudaStream_t st);
+// FP32 leading eigenvectors of L (n x n, n <= 128, r <= 64) per problem.
+struct EighDesc {
+  const float* L; float* U; float* Ut; double* lam; int* status;
+  int n, r, nlam, pad;
+  const GuardTab* guard;
+};
+cudaError_t launch_eigh_grouped(const EighDesc* desc, int n_prob, int max_n, int max_r,
+                                cudaStream_t st);
 cudaError_t launch_chol_env(float* R, long long sR, const int64_t* r_off, const int32_t* D,
                             int maxD, const unsigned int* amax, long long s_amax, int k0, int nk,
                             int batch, cudaStream_t st);
@@ -194,6 +300,16 @@ struct GTen {
 };
 // Runs ops [a, b) of one level; pre: exclusive prefix of n_elems over all ops
 // of the step (pre[i] .. pre[i+1] are op i's elements).
+// Grouped gather (FP32 path): one problem = ops [a, b) of one bucket's step
+// for one instance, with that instance's pointers.
+struct GatherDesc {
+  const GOp* ops; const GTen* ten; const int32_t* code; const int64_t* pre;
+  const double* raw; const double* inv; const float* S; double* scr; float* Y; float* Yt;
+  int a, b;
+  const GuardTab* guard;
+};
+cudaError_t launch_gather_grouped(const GatherDesc* desc, int n_prob, int64_t max_elems,
+                                  cudaStream_t st);
 template <typename TS, typename TY>
 cudaError_t launch_gather(const GOp* ops, const GTen* ten, const int32_t* code, const int64_t* pre,
                           int a, int b, int64_t n_elems, const double* const* tens,

@@ -319,31 +319,47 @@ __global__ void k_fill_env_root_f32(float* R, long long sR, unsigned int* amax, 
 
 // M_r = P (r x D) . Y (D x d), FP64 accumulation and norm; unit-norm FP32
 // store; log-scale += ln ||M_r||; identity boundary site of the first leg.
-__global__ void __launch_bounds__(256) k_root_f32(const float* P, long long sP, int ldp,
-                                                  const float* Y, long long sY, int r, int D,
-                                                  int d, float* S_root, float* S_first, int d0,
-                                                  long long sS, double* logscale, int* status) {
+__global__ void __launch_bounds__(256) k_root_f32(const float* P_, long long sP, int ldp_,
+                                                  const float* Y_, long long sY, int r_, int D_,
+                                                  int d_, float* S_root_, float* S_first_, int d0_,
+                                                  long long sS, double* logscale_, int* status_,
+                                                  const RootDesc* __restrict__ desc) {
   __shared__ double red[32];
   extern __shared__ double mr[];
-  const int i = blockIdx.x;
-  const float* Pi = P + (long long)i * sP;
-  const float* Yi = Y + (long long)i * sY;
+  // grouped launch: block i runs problem desc[i] with its own pointers and
+  // shape; else instance blockIdx.x of the strided arguments
+  const RootDesc* q = desc ? desc + blockIdx.x : nullptr;
+  const GuardTab* gd = q ? q->guard : nullptr;
+  const int i = q ? 0 : int(blockIdx.x);
+  const float* Pi = q ? q->P : P_ + (long long)i * sP;
+  const float* Yi = q ? q->Y : Y_ + (long long)i * sY;
+  float* Si = q ? q->S_root : S_root_ + (long long)i * sS;
+  float* Fi = q ? q->S_first : S_first_ + (long long)i * sS;
+  double* logscale = q ? q->logscale : logscale_;
+  int* status = q ? q->status : status_;
+  const int ldp = q ? q->ldp : ldp_, r = q ? q->r : r_, D = q ? q->D : D_, d = q ? q->d : d_;
+  const int d0 = q ? q->d0 : d0_;
   double ss = 0.0;
   for (int o = threadIdx.x; o < r * d; o += blockDim.x) {
     const int a = o / d, e = o % d;
     double acc = 0.0;
-    for (int k = 0; k < D; ++k)
-      acc = fma((double)Pi[(long long)a * ldp + k], (double)Yi[(long long)k * d + e], acc);
+    for (int k = 0; k < D; ++k) {
+      const float* pp = Pi + (long long)a * ldp + k;
+      const float* py = Yi + (long long)k * d + e;
+      if (guard_ok(gd, pp, 4, 0x701) && guard_ok(gd, py, 4, 0x702))
+        acc = fma((double)*pp, (double)*py, acc);
+    }
     mr[o] = acc;
     ss = fma(acc, acc, ss);
   }
   const double nrm = sqrt(block_sum_d(ss, red));
   const double inv = (nrm > 0.0) ? 1.0 / nrm : 0.0;
-  float* Si = S_root + (long long)i * sS;
-  for (int o = threadIdx.x; o < r * d; o += blockDim.x) Si[o] = float(mr[o] * inv);
-  float* Fi = S_first + (long long)i * sS;
-  for (int o = threadIdx.x; o < d0 * d0; o += blockDim.x) Fi[o] = (o / d0 == o % d0) ? 1.f : 0.f;
-  if (threadIdx.x == 0) {
+  for (int o = threadIdx.x; o < r * d; o += blockDim.x)
+    if (guard_ok(gd, Si + o, 4, 0x703)) Si[o] = float(mr[o] * inv);
+  for (int o = threadIdx.x; o < d0 * d0; o += blockDim.x)
+    if (guard_ok(gd, Fi + o, 4, 0x704)) Fi[o] = (o / d0 == o % d0) ? 1.f : 0.f;
+  if (threadIdx.x == 0 && guard_ok(gd, status + i, 4, 0x705) &&
+      guard_ok(gd, logscale + i, 8, 0x706)) {
     if (!(nrm > 0.0) || !isfinite(nrm)) {
       if (status[i] == TN_OK) status[i] = TN_ERR_NONFINITE;
     } else {
@@ -438,40 +454,69 @@ __global__ void __launch_bounds__(256) k_sgemm_nt(TcGemmArgs g) {
 // then accurate to a few eps of sqrt(sum of squared terms), like an FP64
 // accumulation of the FP32 products, at four FP32 operations per term.
 constexpr int kSgT = 64, kSgK = 16;
+// desc != NULL: grouped launch, blockIdx.z = problem (its own pointers and
+// shape); tiles beyond a problem's extent return at once.
 template <bool kComp>
-__global__ void __launch_bounds__(256) k_sgemm_ffma(TcGemmArgs g) {
+__global__ void __launch_bounds__(256) k_sgemm_ffma(TcGemmArgs g_in,
+                                                    const GemmDesc* __restrict__ desc) {
   __shared__ float As[kSgK][kSgT + 4];
   __shared__ float Bs[kSgK][kSgT + 4];
   __shared__ float red[8];
-  const int i = blockIdx.z;
+  // the problem's operands: its descriptor (grouped launch, blockIdx.z =
+  // problem) or batch entry blockIdx.z of the strided arguments
+  const int z = blockIdx.z;
+  const GemmDesc* dz = desc ? desc + z : nullptr;
+  const GuardTab* gd = dz ? dz->guard : nullptr;
+  const int M = dz ? dz->M : g_in.M;
+  const int N = dz ? dz->N : g_in.N;
+  const int K = dz ? dz->K : g_in.K;
+  const int lda = dz ? dz->lda : g_in.lda;
+  const int ldb = dz ? dz->ldb : g_in.ldb;
+  const int ldc = dz ? dz->ldc : g_in.ldc;
+  const int ldct = dz ? dz->ldct : g_in.ldct;
+  const int ct_cols = dz ? dz->ct_cols : g_in.ct_cols;
+  const float* A = dz ? dz->A : g_in.A + (long long)z * g_in.sA;
+  const float* B = dz ? dz->B : g_in.B + (long long)z * g_in.sB;
+  float* C = dz ? dz->C : (g_in.C ? g_in.C + (long long)z * g_in.sC : nullptr);
+  float* Ct = dz ? dz->Ct : (g_in.Ct ? g_in.Ct + (long long)z * g_in.sCt : nullptr);
+  const unsigned int* amax_in =
+      dz ? dz->amax_in : (g_in.amax_in ? g_in.amax_in + (long long)z * g_in.s_amax_in : nullptr);
+  unsigned int* amax_out =
+      dz ? dz->amax_out
+         : (g_in.amax_out ? g_in.amax_out + (long long)z * g_in.s_amax_out : nullptr);
   const int m0 = blockIdx.y * kSgT, n0 = blockIdx.x * kSgT;
+  if (m0 >= M || n0 >= N) return;  // uniform per block
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const float* A = g.A + (long long)i * g.sA;
-  const float* B = g.B + (long long)i * g.sB;
-  const bool vec = (g.lda % 4 == 0) && (g.ldb % 4 == 0) && (g.sA % 4 == 0) && (g.sB % 4 == 0) &&
-                   (reinterpret_cast<uintptr_t>(g.A) % 16 == 0) &&
-                   (reinterpret_cast<uintptr_t>(g.B) % 16 == 0);
+  const bool vec = (lda % 4 == 0) && (ldb % 4 == 0) &&
+                   (reinterpret_cast<uintptr_t>(A) % 16 == 0) &&
+                   (reinterpret_cast<uintptr_t>(B) % 16 == 0);
   const int lr = tid >> 2, lk = (tid & 3) * 4;  // loader: row, first k of its 4
   float acc[4][4], cmp[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int v = 0; v < 4; ++v) acc[u][v] = cmp[u][v] = 0.f;
-  for (int k0 = 0; k0 < g.K; k0 += kSgK) {
+  for (int k0 = 0; k0 < K; k0 += kSgK) {
     float av[4], bv[4];
     const int am = m0 + lr, bn = n0 + lr, kk = k0 + lk;
-    if (vec && kk + 3 < g.K) {
-      const float4 a4 = (am < g.M) ? *reinterpret_cast<const float4*>(A + (long long)am * g.lda + kk)
-                                   : make_float4(0.f, 0.f, 0.f, 0.f);
-      const float4 b4 = (bn < g.N) ? *reinterpret_cast<const float4*>(B + (long long)bn * g.ldb + kk)
-                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (vec && kk + 3 < K) {
+      const float* pa = A + (long long)am * lda + kk;
+      const float* pb = B + (long long)bn * ldb + kk;
+      const float4 a4 = (am < M && guard_ok(gd, pa, 16, 0x201))
+                            ? *reinterpret_cast<const float4*>(pa)
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 b4 = (bn < N && guard_ok(gd, pb, 16, 0x202))
+                            ? *reinterpret_cast<const float4*>(pb)
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
       av[0] = a4.x; av[1] = a4.y; av[2] = a4.z; av[3] = a4.w;
       bv[0] = b4.x; bv[1] = b4.y; bv[2] = b4.z; bv[3] = b4.w;
     } else {
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        av[q] = (am < g.M && kk + q < g.K) ? A[(long long)am * g.lda + kk + q] : 0.f;
-        bv[q] = (bn < g.N && kk + q < g.K) ? B[(long long)bn * g.ldb + kk + q] : 0.f;
+        const float* pa = A + (long long)am * lda + kk + q;
+        const float* pb = B + (long long)bn * ldb + kk + q;
+        av[q] = (am < M && kk + q < K && guard_ok(gd, pa, 4, 0x203)) ? *pa : 0.f;
+        bv[q] = (bn < N && kk + q < K && guard_ok(gd, pb, 4, 0x204)) ? *pb : 0.f;
       }
     }
     __syncthreads();  // the previous chunk's reads are done
@@ -502,36 +547,38 @@ __global__ void __launch_bounds__(256) k_sgemm_ffma(TcGemmArgs g) {
     }
   }
   float alpha = 1.f;
-  if (g.amax_in) {
-    const float mx = __uint_as_float(g.amax_in[(long long)i * g.s_amax_in]);
+  if (amax_in && guard_ok(gd, amax_in, 4, 0x207)) {
+    const float mx = __uint_as_float(*amax_in);
     alpha = (mx > 0.f) ? 1.f / mx : 1.f;
   }
   float lmax = 0.f;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int m = m0 + 4 * ty + u;
-    if (m >= g.M) continue;
+    if (m >= M) continue;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       const int n = n0 + 4 * tx + v;
-      if (n >= g.N) continue;
+      if (n >= N) continue;
       const float x = acc[u][v] * alpha;
-      if (g.C) g.C[(long long)i * g.sC + (long long)m * g.ldc + n] = x;
-      if (g.Ct) {
-        const int q = n / g.ct_cols, cc = n - q * g.ct_cols;
-        g.Ct[(long long)i * g.sCt + (long long)cc * g.ldct + (long long)m * (g.N / g.ct_cols) + q] = x;
+      float* pc = C ? C + (long long)m * ldc + n : nullptr;
+      if (pc && guard_ok(gd, pc, 4, 0x205)) *pc = x;
+      if (Ct) {
+        const int q = n / ct_cols, cc = n - q * ct_cols;
+        float* pt = Ct + (long long)cc * ldct + (long long)m * (N / ct_cols) + q;
+        if (guard_ok(gd, pt, 4, 0x206)) *pt = x;
       }
       lmax = fmaxf(lmax, isfinite(x) ? fabsf(x) : INFINITY);
     }
   }
-  if (g.amax_out) {
+  if (amax_out) {
     for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
     if ((tid & 31) == 0) red[tid >> 5] = lmax;
     __syncthreads();
     if (tid == 0) {
       float v = red[0];
       for (int w = 1; w < 8; ++w) v = fmaxf(v, red[w]);
-      atomicMax(g.amax_out + (long long)i * g.s_amax_out, __float_as_uint(v));
+      if (guard_ok(gd, amax_out, 4, 0x208)) atomicMax(amax_out, __float_as_uint(v));
     }
   }
 }
@@ -551,8 +598,20 @@ cudaError_t launch_sgemm_ffma(const TcGemmArgs& g, bool compensated, cudaStream_
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
   if (g.Ct && (g.ct_cols <= 0 || g.N % g.ct_cols)) return cudaErrorInvalidValue;
   dim3 grid(unsigned((g.N + kSgT - 1) / kSgT), unsigned((g.M + kSgT - 1) / kSgT), g.batch);
-  if (compensated) k_sgemm_ffma<true><<<grid, 256, 0, st>>>(g);
-  else k_sgemm_ffma<false><<<grid, 256, 0, st>>>(g);
+  if (compensated) k_sgemm_ffma<true><<<grid, 256, 0, st>>>(g, nullptr);
+  else k_sgemm_ffma<false><<<grid, 256, 0, st>>>(g, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_grouped(const GemmDesc* desc, int n_prob, int max_M, int max_N,
+                                bool compensated, cudaStream_t st) {
+  if (n_prob <= 0 || max_M <= 0 || max_N <= 0) return cudaSuccess;
+  if (n_prob > 65535) return cudaErrorInvalidValue;
+  TcGemmArgs g{};
+  dim3 grid(unsigned((max_N + kSgT - 1) / kSgT), unsigned((max_M + kSgT - 1) / kSgT),
+            unsigned(n_prob));
+  if (compensated) k_sgemm_ffma<true><<<grid, 256, 0, st>>>(g, desc);
+  else k_sgemm_ffma<false><<<grid, 256, 0, st>>>(g, desc);
   return cudaGetLastError();
 }
 
@@ -596,7 +655,34 @@ cudaError_t launch_root_f32(const float* P, long long sP, int ldp, const float* 
                             cudaStream_t st) {
   const size_t smem = sizeof(double) * size_t(r) * d;
   k_root_f32<<<batch, 256, smem, st>>>(P, sP, ldp, Y, sY, r, D, d, S_root, S_first, d0, sS,
-                                       logscale, status);
+                                       logscale, status, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_root_grouped(const RootDesc* desc, int n_prob, int max_rd, cudaStream_t st) {
+  if (n_prob <= 0) return cudaSuccess;
+  const size_t smem = sizeof(double) * size_t(max_rd);
+  if (smem > 48 * 1024) return cudaErrorInvalidValue;
+  k_root_f32<<<n_prob, 256, smem, st>>>(nullptr, 0, 0, nullptr, 0, 0, 0, 0, nullptr, nullptr, 0,
+                                        0, nullptr, nullptr, desc);
+  return cudaGetLastError();
+}
+
+namespace {
+__global__ void k_env_root_grouped(const EnvRootDesc* __restrict__ desc, int n_prob) {
+  const int p = blockIdx.x;
+  if (p >= n_prob) return;
+  const EnvRootDesc q = desc[p];
+  for (int k = threadIdx.x; k < q.n; k += blockDim.x)
+    if (guard_ok(q.guard, q.amax + k, 4, 0x101))
+      q.amax[k] = (k == q.n - 1) ? __float_as_uint(1.0f) : 0u;
+  if (threadIdx.x == 0 && guard_ok(q.guard, q.R, 4, 0x102)) q.R[0] = 1.0f;
+}
+}  // namespace
+
+cudaError_t launch_env_root_grouped(const EnvRootDesc* desc, int n_prob, cudaStream_t st) {
+  if (n_prob <= 0) return cudaSuccess;
+  k_env_root_grouped<<<n_prob, 64, 0, st>>>(desc, n_prob);
   return cudaGetLastError();
 }
 

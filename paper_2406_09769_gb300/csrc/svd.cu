@@ -81,15 +81,28 @@ __global__ void __launch_bounds__(kThreads, 2) k_chol_env(float* __restrict__ R,
                                                           const int64_t* __restrict__ r_off,
                                                           const int32_t* __restrict__ D,
                                                           const unsigned int* __restrict__ amax,
-                                                          long long s_amax, int k0, int nk) {
+                                                          long long s_amax, int k0, int nk,
+                                                          const CholDesc* __restrict__ desc) {
   __shared__ __align__(16) float Xc[128];
   __shared__ float dg[128];
   __shared__ int dn[128];
-  const int b = blockIdx.x / nk;
-  const int k = k0 + blockIdx.x % nk;
-  const int n = D[k];
-  float* Rg = R + (long long)b * sR + r_off[k];
-  const float am = __uint_as_float(amax[(long long)b * s_amax + k]);
+  int n;
+  float* Rg;
+  float am;
+  const GuardTab* gd = nullptr;
+  if (desc) {  // grouped launch: CTA i factors problem desc[i]
+    const CholDesc d = desc[blockIdx.x];
+    gd = d.guard;
+    n = d.n;
+    Rg = d.R;
+    am = guard_ok(gd, d.amax, 4, 0x401) ? __uint_as_float(*d.amax) : 1.f;
+  } else {
+    const int b = blockIdx.x / nk;
+    const int k = k0 + blockIdx.x % nk;
+    n = D[k];
+    Rg = R + (long long)b * sR + r_off[k];
+    am = __uint_as_float(amax[(long long)b * s_amax + k]);
+  }
   const float sc = (am > 0.f && isfinite(am)) ? 0.5f / am : 0.5f;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ta = 2 * warp + (lane >> 4), tb = lane & 15;
@@ -100,8 +113,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_chol_env(float* __restrict__ R,
 #pragma unroll
     for (int jj = 0; jj < 8; ++jj) {
       const int i = r0 + ii, c = c0 + jj;
-      t[ii][jj] = (i < n && c < n) ? (Rg[(long long)i * n + c] + Rg[(long long)c * n + i]) * sc
-                                   : 0.f;
+      t[ii][jj] = (i < n && c < n && guard_ok(gd, Rg + (long long)i * n + c, 4, 0x402) &&
+                   guard_ok(gd, Rg + (long long)c * n + i, 4, 0x402))
+                      ? (Rg[(long long)i * n + c] + Rg[(long long)c * n + i]) * sc
+                      : 0.f;
     }
   if (tid < 128) dn[tid] = 0;
   __syncthreads();  // every load of R_k done before the first store of C^T
@@ -137,7 +152,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_chol_env(float* __restrict__ R,
     // needs; dropping them biases which subspace the next vertices keep.
     const bool ok = isfinite(pv) && pv > FLT_EPSILON * FLT_EPSILON * first && pv > 0.f;
     if (!ok) {
-      for (long long q = (long long)j * n + tid; q < (long long)n * n; q += kThreads) Rg[q] = 0.f;
+      for (long long q = (long long)j * n + tid; q < (long long)n * n; q += kThreads)
+        if (guard_ok(gd, Rg + q, 4, 0x403)) Rg[q] = 0.f;
       break;
     }
     if (tb == (pi >> 3)) {
@@ -162,7 +178,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_chol_env(float* __restrict__ R,
       float v = 0.f;
       if (l == pi) v = pv * rs;
       else if (!dn[l]) v = Xc[l] * rs;
-      Rg[(long long)j * n + l] = v;
+      if (guard_ok(gd, Rg + (long long)j * n + l, 4, 0x404)) Rg[(long long)j * n + l] = v;
     }
     // rank-1 update of the whole tile (eliminated rows and columns are never
     // read again)
@@ -285,14 +301,27 @@ __device__ __forceinline__ float half_sum(float v) {
   return v;
 }
 
-__global__ void __launch_bounds__(kThreads, 2) k_svd_left(const float* __restrict__ Kg,
-                                                           long long sK, int m, int n,
-                                                           float* __restrict__ Ug, long long sU,
-                                                           float* __restrict__ Utg, long long sUt,
-                                                           double* __restrict__ lamg,
-                                                           long long slam, int r, int nlam,
-                                                           int* __restrict__ status, int rounds) {
+// desc != NULL: grouped launch, CTA i takes problem desc[i] (its own pointers and
+// shape; the strided arguments are ignored).
+__global__ void __launch_bounds__(kThreads, 2) k_svd_left(const float* __restrict__ Kg_,
+                                                           long long sK, int m_, int n_,
+                                                           float* __restrict__ Ug_, long long sU,
+                                                           float* __restrict__ Utg_, long long sUt,
+                                                           double* __restrict__ lamg_,
+                                                           long long slam, int r_, int nlam_,
+                                                           int* __restrict__ status_, int rounds,
+                                                           const SvdDesc* __restrict__ desc) {
   extern __shared__ __align__(16) float sm[];
+  const SvdDesc* dq = desc ? desc + blockIdx.x : nullptr;
+  const GuardTab* gd = dq ? dq->guard : nullptr;
+  const float* Kg = dq ? dq->K : Kg_;
+  float* Ug = dq ? dq->U : Ug_;
+  float* Utg = dq ? dq->Ut : Utg_;
+  double* lamg = dq ? dq->lam : lamg_;
+  int* status = dq ? dq->status : status_;
+  const int m = dq ? dq->m : m_, n = dq ? dq->n : n_, r = dq ? dq->r : r_;
+  const int nlam = dq ? dq->nlam : nlam_;
+  const int b = dq ? 0 : int(blockIdx.x);
   const int p = m < n ? m : n;
   const int N = (m < n) ? 2 * p + 1 : 2 * p;
   const int mr = (m + 3) & ~3;
@@ -314,7 +343,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_svd_left(const float* __restric
   int* roff = reinterpret_cast<int*>(scal + 16);      // 132: reflector offsets
   float* Zb = reinterpret_cast<float*>(roff + 132);   // 128: per-warp row sums
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int b = blockIdx.x;
   const int ta = 2 * warp + (lane >> 4), tb = lane & 15;
   const int r0 = 8 * ta, c0 = 8 * tb;
   const float* K = Kg + (long long)b * sK;
@@ -327,7 +355,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_svd_left(const float* __restric
 #pragma unroll
     for (int jj = 0; jj < 8; ++jj) {
       const int row = r0 + ii, col = c0 + jj;
-      const float x = (row < m && col < n) ? K[(long long)row * n + col] : 0.f;
+      const float x = (row < m && col < n && guard_ok(gd, K + (long long)row * n + col, 4, 0x501))
+                          ? K[(long long)row * n + col]
+                          : 0.f;
       if (!isfinite(x)) bad = true;
       kt[ii][jj] = x;
     }
@@ -339,12 +369,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_svd_left(const float* __restric
     }
   }
   if (__syncthreads_or(bad)) {
-    for (int idx = tid; idx < m * r; idx += kThreads) Ug[(long long)b * sU + idx] = 0.f;
+    for (int idx = tid; idx < m * r; idx += kThreads)
+      if (guard_ok(gd, Ug + (long long)b * sU + idx, 4, 0x502)) Ug[(long long)b * sU + idx] = 0.f;
     if (Utg)
-      for (int idx = tid; idx < m * r; idx += kThreads) Utg[(long long)b * sUt + idx] = 0.f;
+      for (int idx = tid; idx < m * r; idx += kThreads)
+        if (guard_ok(gd, Utg + (long long)b * sUt + idx, 4, 0x503))
+          Utg[(long long)b * sUt + idx] = 0.f;
     if (lamg)
-      for (int t = tid; t < nlam; t += kThreads) lamg[(long long)b * slam + t] = 0.0;
-    if (tid == 0) status[b] = TN_ERR_NONFINITE;
+      for (int t = tid; t < nlam; t += kThreads)
+        if (guard_ok(gd, lamg + (long long)b * slam + t, 8, 0x504))
+          lamg[(long long)b * slam + t] = 0.0;
+    if (tid == 0 && guard_ok(gd, status + b, 4, 0x505)) status[b] = TN_ERR_NONFINITE;
     return;
   }
   // publish column 0 and row 0
@@ -649,7 +684,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_svd_left(const float* __restric
       }
       if (valid && q == 0) {
         lam[t] = fmaxf(0.5f * (lo + hi), 0.f);
-        if (hi - lo > 128.f * eps * tnorm) atomicCAS(status + b, 0, int(TN_ERR_EIG_NOCONV));
+        if (hi - lo > 128.f * eps * tnorm && guard_ok(gd, status + b, 4, 0x506))
+          atomicCAS(status + b, 0, int(TN_ERR_EIG_NOCONV));
       }
     }
   }
@@ -860,8 +896,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_svd_left(const float* __restric
     for (int kk = 0; kk < kQ; ++kk) {
       const int row = 32 * qr + kk;
       if (row < m) {
-        U[(long long)row * r + col] = sg * z[kk];
-        if (Ut) Ut[row] = sg * z[kk];
+        if (guard_ok(gd, U + (long long)row * r + col, 4, 0x507))
+          U[(long long)row * r + col] = sg * z[kk];
+        if (Ut && guard_ok(gd, Ut + row, 4, 0x508)) Ut[row] = sg * z[kk];
       }
     }
   }
@@ -869,7 +906,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_svd_left(const float* __restric
     double* lo = lamg + (long long)b * slam;
     for (int t = tid; t < nlam; t += kThreads) {
       const double sv = (t < nl) ? double(lam[t]) : 0.0;
-      lo[t] = sv * sv;
+      if (guard_ok(gd, lo + t, 8, 0x509)) lo[t] = sv * sv;
     }
   }
 }
@@ -880,7 +917,13 @@ cudaError_t launch_chol_env(float* R, long long sR, const int64_t* r_off, const 
                             int maxD, const unsigned int* amax, long long s_amax, int k0, int nk,
                             int batch, cudaStream_t st) {
   if (maxD < 1 || maxD > kNmax || nk < 1) return cudaErrorInvalidValue;
-  k_chol_env<<<batch * nk, kThreads, 0, st>>>(R, sR, r_off, D, amax, s_amax, k0, nk);
+  k_chol_env<<<batch * nk, kThreads, 0, st>>>(R, sR, r_off, D, amax, s_amax, k0, nk, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chol_grouped(const CholDesc* desc, int n_prob, cudaStream_t st) {
+  if (n_prob <= 0) return cudaSuccess;
+  k_chol_env<<<n_prob, kThreads, 0, st>>>(nullptr, 0, nullptr, nullptr, nullptr, 0, 0, 1, desc);
   return cudaGetLastError();
 }
 
@@ -902,7 +945,18 @@ cudaError_t launch_svd_left(const float* K, long long sK, int m, int n, float* U
     return cudaErrorInvalidValue;
   const size_t smem = svd_left_smem_bytes(m, n, r);
   k_svd_left<<<batch, kThreads, smem, st>>>(K, sK, m, n, U, sU, Ut, sUt, lam, slam, r, nlam,
-                                            status, rounds);
+                                            status, rounds, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_svd_left_grouped(const SvdDesc* desc, int n_prob, int max_m, int max_n,
+                                    int max_r, cudaStream_t st, int rounds) {
+  if (n_prob <= 0) return cudaSuccess;
+  if (!svd_left_supported(max_m, max_n, max_r) || rounds < 1 || rounds > 16)
+    return cudaErrorInvalidValue;
+  const size_t smem = svd_left_smem_bytes(max_m, max_n, max_r);
+  k_svd_left<<<n_prob, kThreads, smem, st>>>(nullptr, 0, 0, 0, nullptr, 0, nullptr, 0, nullptr, 0,
+                                             0, 0, nullptr, rounds, desc);
   return cudaGetLastError();
 }
 
