@@ -1511,7 +1511,7 @@ void run_grouped_tc(tn_ctx* c, const std::vector<Bucket>& bks, bool factored, bo
       case 3:
         Scope(c, g.cls, strm),
         ck(tn::launch_gemm_grouped(reinterpret_cast<tn::GemmDesc*>(d), g.count, int(g.p0),
-                                   int(g.p1), g.kind == 3 && c->value_comp, strm),
+                                   int(g.p1), g.kind == 3 && c->value_comp, guard_mode, strm),
            "grouped gemm");
         break;
       case 4:

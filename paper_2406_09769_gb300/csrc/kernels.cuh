@@ -258,7 +258,7 @@ cudaError_t launch_svd_left_grouped(const SvdDesc* desc, int n_prob, int max_m, 
                                     int max_r, cudaStream_t st, int rounds = 9);
 cudaError_t launch_chol_grouped(const CholDesc* desc, int n_prob, cudaStream_t st);
 cudaError_t launch_gemm_grouped(const GemmDesc* desc, int n_prob, int max_M, int max_N,
-                                bool compensated, cudaStream_t st);
+                                bool compensated, bool guarded, cudaStream_t st);
 cudaError_t launch_root_grouped(const RootDesc* desc, int n_prob, int max_rd, cudaStream_t st);
 cudaError_t launch_env_root_grouped(const EnvRootDesc* desc, int n_prob, cudaStream_t st);
 // FP32 leading eigenvectors of L (n x n, n <= 128, r <= 64) per problem.

@@ -454,9 +454,11 @@ __global__ void __launch_bounds__(256) k_sgemm_nt(TcGemmArgs g) {
 // then accurate to a few eps of sqrt(sum of squared terms), like an FP64
 // accumulation of the FP32 products, at four FP32 operations per term.
 constexpr int kSgT = 64, kSgK = 16;
-// desc != NULL: grouped launch, blockIdx.z = problem (its own pointers and
-// shape); tiles beyond a problem's extent return at once.
-template <bool kComp>
+// kMode 0: batch of strided problems (blockIdx.z = instance of g_in);
+// 1: grouped launch, blockIdx.z = problem desc[z] with its own pointers and
+// shape (tiles beyond a problem's extent return at once); 2: as 1 with the
+// range guard of the descriptors checked on every global access.
+template <bool kComp, int kMode>
 __global__ void __launch_bounds__(256) k_sgemm_ffma(TcGemmArgs g_in,
                                                     const GemmDesc* __restrict__ desc) {
   __shared__ float As[kSgK][kSgT + 4];
@@ -465,8 +467,8 @@ __global__ void __launch_bounds__(256) k_sgemm_ffma(TcGemmArgs g_in,
   // the problem's operands: its descriptor (grouped launch, blockIdx.z =
   // problem) or batch entry blockIdx.z of the strided arguments
   const int z = blockIdx.z;
-  const GemmDesc* dz = desc ? desc + z : nullptr;
-  const GuardTab* gd = dz ? dz->guard : nullptr;
+  const GemmDesc* dz = kMode ? desc + z : nullptr;
+  const GuardTab* gd = kMode == 2 ? dz->guard : nullptr;
   const int M = dz ? dz->M : g_in.M;
   const int N = dz ? dz->N : g_in.N;
   const int K = dz ? dz->K : g_in.K;
@@ -598,20 +600,25 @@ cudaError_t launch_sgemm_ffma(const TcGemmArgs& g, bool compensated, cudaStream_
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
   if (g.Ct && (g.ct_cols <= 0 || g.N % g.ct_cols)) return cudaErrorInvalidValue;
   dim3 grid(unsigned((g.N + kSgT - 1) / kSgT), unsigned((g.M + kSgT - 1) / kSgT), g.batch);
-  if (compensated) k_sgemm_ffma<true><<<grid, 256, 0, st>>>(g, nullptr);
-  else k_sgemm_ffma<false><<<grid, 256, 0, st>>>(g, nullptr);
+  if (compensated) k_sgemm_ffma<true, 0><<<grid, 256, 0, st>>>(g, nullptr);
+  else k_sgemm_ffma<false, 0><<<grid, 256, 0, st>>>(g, nullptr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gemm_grouped(const GemmDesc* desc, int n_prob, int max_M, int max_N,
-                                bool compensated, cudaStream_t st) {
+                                bool compensated, bool guarded, cudaStream_t st) {
   if (n_prob <= 0 || max_M <= 0 || max_N <= 0) return cudaSuccess;
   if (n_prob > 65535) return cudaErrorInvalidValue;
   TcGemmArgs g{};
   dim3 grid(unsigned((max_N + kSgT - 1) / kSgT), unsigned((max_M + kSgT - 1) / kSgT),
             unsigned(n_prob));
-  if (compensated) k_sgemm_ffma<true><<<grid, 256, 0, st>>>(g, desc);
-  else k_sgemm_ffma<false><<<grid, 256, 0, st>>>(g, desc);
+  if (guarded) {
+    if (compensated) k_sgemm_ffma<true, 2><<<grid, 256, 0, st>>>(g, desc);
+    else k_sgemm_ffma<false, 2><<<grid, 256, 0, st>>>(g, desc);
+  } else {
+    if (compensated) k_sgemm_ffma<true, 1><<<grid, 256, 0, st>>>(g, desc);
+    else k_sgemm_ffma<false, 1><<<grid, 256, 0, st>>>(g, desc);
+  }
   return cudaGetLastError();
 }
 
