@@ -1499,7 +1499,8 @@ void run_grouped_tc(tn_ctx* c, const std::vector<Bucket>& bks, bool factored, bo
     switch (g.kind) {
       case 0:
         Scope(c, g.cls, strm),
-        ck(tn::launch_gather_grouped(reinterpret_cast<tn::GatherDesc*>(d), g.count, g.p0, strm),
+        ck(tn::launch_gather_grouped(reinterpret_cast<tn::GatherDesc*>(d), g.count, g.p0, guard_mode,
+                                     strm),
            "grouped gather");
         break;
       case 1:
@@ -1516,24 +1517,25 @@ void run_grouped_tc(tn_ctx* c, const std::vector<Bucket>& bks, bool factored, bo
         break;
       case 4:
         Scope(c, g.cls, strm),
-        ck(tn::launch_chol_grouped(reinterpret_cast<tn::CholDesc*>(d), g.count, strm),
+        ck(tn::launch_chol_grouped(reinterpret_cast<tn::CholDesc*>(d), g.count, guard_mode, strm),
            "grouped cholesky");
         break;
       case 5:
         Scope(c, g.cls, strm),
         ck(tn::launch_svd_left_grouped(reinterpret_cast<tn::SvdDesc*>(d), g.count, int(g.p0),
-                                       int(g.p1), int(g.p2), strm, c->eig_rounds),
+                                       int(g.p1), int(g.p2), guard_mode, strm, c->eig_rounds),
            "grouped svd");
         break;
       case 6:
         Scope(c, g.cls, strm),
         ck(tn::launch_eigh_grouped(reinterpret_cast<tn::EighDesc*>(d), g.count, int(g.p0),
-                                   int(g.p1), strm),
+                                   int(g.p1), guard_mode, strm),
            "grouped eigh");
         break;
       case 7:
         Scope(c, g.cls, strm),
-        ck(tn::launch_root_grouped(reinterpret_cast<tn::RootDesc*>(d), g.count, int(g.p0), strm),
+        ck(tn::launch_root_grouped(reinterpret_cast<tn::RootDesc*>(d), g.count, int(g.p0), guard_mode,
+                                   strm),
            "grouped root");
         break;
       case 8: {

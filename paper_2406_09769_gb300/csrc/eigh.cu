@@ -679,8 +679,9 @@ __host__ __device__ __forceinline__ int fast_region_a(int n) {
   return m > rr ? m : rr;
 }
 
-// desc != NULL (FP32 only): grouped launch, CTA i solves problem desc[i].
-template <typename T>
+// kMode 0: strided batch; 1 (FP32 only): grouped launch, CTA i solves problem
+// desc[i]; 2: as 1 with the range guard checked on every global access.
+template <typename T, int kMode = 0>
 __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg_, long long sL,
                                                         T* __restrict__ Ug_, long long sU,
                                                         T* __restrict__ Utg_, long long sUt,
@@ -691,8 +692,8 @@ __global__ void __launch_bounds__(kThreads) k_eigh_fast(const T* __restrict__ Lg
   __shared__ T scal[8];
   // grouped launch: CTA i solves problem desc[i] with its own pointers and
   // shape; else instance blockIdx.x of the strided arguments
-  const EighDesc* qd = desc ? desc + blockIdx.x : nullptr;
-  const GuardTab* gd = qd ? qd->guard : nullptr;
+  const EighDesc* qd = kMode ? desc + blockIdx.x : nullptr;
+  const GuardTab* gd = kMode == 2 ? qd->guard : nullptr;
   const int b = qd ? 0 : int(blockIdx.x);
   const T* Lg = qd ? reinterpret_cast<const T*>(qd->L) : Lg_;
   T* Ug = qd ? reinterpret_cast<T*>(qd->U) : Ug_;
@@ -1151,7 +1152,8 @@ cudaError_t launch_eigh_top(const T* L, long long sL, T* U, long long sU, T* Ut,
 }
 
 namespace {
-size_t g_limit[4] = {0, 0, 0, 0};  // top<double>, top<float>, fast<double>, fast<float>
+size_t g_limit[5] = {0, 0, 0, 0, 0};  // top<double>, top<float>, fast<double>, fast<float>,
+                                      // fast<float> grouped
 
 template <typename K>
 cudaError_t configure_kernel(K kern, size_t* out) {
@@ -1188,17 +1190,22 @@ cudaError_t eigh_configure() {
   if (e == cudaSuccess) e = configure_kernel(k_eigh_top<float, float>, &g_limit[1]);
   if (e == cudaSuccess) e = configure_kernel(k_eigh_fast<double>, &g_limit[2]);
   if (e == cudaSuccess) e = configure_kernel(k_eigh_fast<float>, &g_limit[3]);
+  size_t lim1 = 0, lim2 = 0;
+  if (e == cudaSuccess) e = configure_kernel(k_eigh_fast<float, 1>, &lim1);
+  if (e == cudaSuccess) e = configure_kernel(k_eigh_fast<float, 2>, &lim2);
+  if (e == cudaSuccess) g_limit[4] = std::min(lim1, lim2);
   return e;
 }
 
 cudaError_t launch_eigh_grouped(const EighDesc* desc, int n_prob, int max_n, int max_r,
-                                cudaStream_t st) {
+                                bool guarded, cudaStream_t st) {
   if (n_prob <= 0) return cudaSuccess;
   if (max_n < 1 || max_n > kNmax || max_r < 1 || max_r > 64) return cudaErrorInvalidValue;
   const size_t smem = eigh_fast_smem_bytes<float>(max_n, max_r);
-  if (smem > eigh_fast_smem_limit<float>()) return cudaErrorInvalidValue;
-  k_eigh_fast<float><<<n_prob, kThreads, smem, st>>>(nullptr, 0, nullptr, 0, nullptr, 0, nullptr,
-                                                     0, 0, 0, 0, nullptr, desc);
+  if (smem > g_limit[4]) return cudaErrorInvalidValue;
+  auto kern = guarded ? k_eigh_fast<float, 2> : k_eigh_fast<float, 1>;
+  kern<<<n_prob, kThreads, smem, st>>>(nullptr, 0, nullptr, 0, nullptr, 0, nullptr, 0, 0, 0, 0,
+                                       nullptr, desc);
   return cudaGetLastError();
 }
 

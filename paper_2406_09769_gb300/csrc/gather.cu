@@ -121,11 +121,13 @@ __global__ void __launch_bounds__(kThreads)
                        Y + inst * sY, Yt ? Yt + inst * sY : nullptr);
 }
 
-// grouped: blockIdx.y = problem (one instance of one bucket at one level)
+// grouped: blockIdx.y = problem (one instance of one bucket at one level);
+// kGuard: the range guard checked on every global access
+template <bool kGuard>
 __global__ void __launch_bounds__(kThreads) k_gather_grouped(const GatherDesc* __restrict__ desc) {
   const GatherDesc q = desc[blockIdx.y];
   gather_range<float, float>(q.ops, q.ten, q.code, q.pre, q.a, q.b, q.raw, q.inv, q.S, q.scr, q.Y,
-                             q.Yt, q.guard);
+                             q.Yt, kGuard ? q.guard : nullptr);
 }
 
 }  // namespace
@@ -145,12 +147,13 @@ cudaError_t launch_gather(const GOp* ops, const GTen* ten, const int32_t* code, 
 }
 
 cudaError_t launch_gather_grouped(const GatherDesc* desc, int n_prob, int64_t max_elems,
-                                  cudaStream_t st) {
+                                  bool guarded, cudaStream_t st) {
   if (n_prob <= 0 || max_elems <= 0) return cudaSuccess;
   if (n_prob > 65535) return cudaErrorInvalidValue;
   const int64_t want = (max_elems + kThreads - 1) / kThreads;
   const int grid = int(want < 64 ? want : 64);
-  k_gather_grouped<<<dim3(grid, n_prob), kThreads, 0, st>>>(desc);
+  if (guarded) k_gather_grouped<true><<<dim3(grid, n_prob), kThreads, 0, st>>>(desc);
+  else k_gather_grouped<false><<<dim3(grid, n_prob), kThreads, 0, st>>>(desc);
   return cudaGetLastError();
 }
 

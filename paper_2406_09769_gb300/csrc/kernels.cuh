@@ -255,11 +255,12 @@ struct EnvRootDesc {
   const GuardTab* guard;
 };
 cudaError_t launch_svd_left_grouped(const SvdDesc* desc, int n_prob, int max_m, int max_n,
-                                    int max_r, cudaStream_t st, int rounds = 9);
-cudaError_t launch_chol_grouped(const CholDesc* desc, int n_prob, cudaStream_t st);
+                                    int max_r, bool guarded, cudaStream_t st, int rounds = 9);
+cudaError_t launch_chol_grouped(const CholDesc* desc, int n_prob, bool guarded, cudaStream_t st);
 cudaError_t launch_gemm_grouped(const GemmDesc* desc, int n_prob, int max_M, int max_N,
                                 bool compensated, bool guarded, cudaStream_t st);
-cudaError_t launch_root_grouped(const RootDesc* desc, int n_prob, int max_rd, cudaStream_t st);
+cudaError_t launch_root_grouped(const RootDesc* desc, int n_prob, int max_rd, bool guarded,
+                                cudaStream_t st);
 cudaError_t launch_env_root_grouped(const EnvRootDesc* desc, int n_prob, cudaStream_t st);
 // FP32 leading eigenvectors of L (n x n, n <= 128, r <= 64) per problem.
 struct EighDesc {
@@ -268,7 +269,7 @@ struct EighDesc {
   const GuardTab* guard;
 };
 cudaError_t launch_eigh_grouped(const EighDesc* desc, int n_prob, int max_n, int max_r,
-                                cudaStream_t st);
+                                bool guarded, cudaStream_t st);
 cudaError_t launch_chol_env(float* R, long long sR, const int64_t* r_off, const int32_t* D,
                             int maxD, const unsigned int* amax, long long s_amax, int k0, int nk,
                             int batch, cudaStream_t st);
@@ -309,7 +310,7 @@ struct GatherDesc {
   const GuardTab* guard;
 };
 cudaError_t launch_gather_grouped(const GatherDesc* desc, int n_prob, int64_t max_elems,
-                                  cudaStream_t st);
+                                  bool guarded, cudaStream_t st);
 template <typename TS, typename TY>
 cudaError_t launch_gather(const GOp* ops, const GTen* ten, const int32_t* code, const int64_t* pre,
                           int a, int b, int64_t n_elems, const double* const* tens,

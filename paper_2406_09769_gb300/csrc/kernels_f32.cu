@@ -319,6 +319,9 @@ __global__ void k_fill_env_root_f32(float* R, long long sR, unsigned int* amax, 
 
 // M_r = P (r x D) . Y (D x d), FP64 accumulation and norm; unit-norm FP32
 // store; log-scale += ln ||M_r||; identity boundary site of the first leg.
+// kMode 0: strided batch; 1: grouped (block i runs problem desc[i]); 2: as 1
+// with the range guard checked on every global access.
+template <int kMode>
 __global__ void __launch_bounds__(256) k_root_f32(const float* P_, long long sP, int ldp_,
                                                   const float* Y_, long long sY, int r_, int D_,
                                                   int d_, float* S_root_, float* S_first_, int d0_,
@@ -328,8 +331,8 @@ __global__ void __launch_bounds__(256) k_root_f32(const float* P_, long long sP,
   extern __shared__ double mr[];
   // grouped launch: block i runs problem desc[i] with its own pointers and
   // shape; else instance blockIdx.x of the strided arguments
-  const RootDesc* q = desc ? desc + blockIdx.x : nullptr;
-  const GuardTab* gd = q ? q->guard : nullptr;
+  const RootDesc* q = kMode ? desc + blockIdx.x : nullptr;
+  const GuardTab* gd = kMode == 2 ? q->guard : nullptr;
   const int i = q ? 0 : int(blockIdx.x);
   const float* Pi = q ? q->P : P_ + (long long)i * sP;
   const float* Yi = q ? q->Y : Y_ + (long long)i * sY;
@@ -661,16 +664,18 @@ cudaError_t launch_root_f32(const float* P, long long sP, int ldp, const float* 
                             long long sS, double* logscale, int* status, int batch,
                             cudaStream_t st) {
   const size_t smem = sizeof(double) * size_t(r) * d;
-  k_root_f32<<<batch, 256, smem, st>>>(P, sP, ldp, Y, sY, r, D, d, S_root, S_first, d0, sS,
+  k_root_f32<0><<<batch, 256, smem, st>>>(P, sP, ldp, Y, sY, r, D, d, S_root, S_first, d0, sS,
                                        logscale, status, nullptr);
   return cudaGetLastError();
 }
 
-cudaError_t launch_root_grouped(const RootDesc* desc, int n_prob, int max_rd, cudaStream_t st) {
+cudaError_t launch_root_grouped(const RootDesc* desc, int n_prob, int max_rd, bool guarded,
+                                cudaStream_t st) {
   if (n_prob <= 0) return cudaSuccess;
   const size_t smem = sizeof(double) * size_t(max_rd);
   if (smem > 48 * 1024) return cudaErrorInvalidValue;
-  k_root_f32<<<n_prob, 256, smem, st>>>(nullptr, 0, 0, nullptr, 0, 0, 0, 0, nullptr, nullptr, 0,
+  auto kern = guarded ? k_root_f32<2> : k_root_f32<1>;
+  kern<<<n_prob, 256, smem, st>>>(nullptr, 0, 0, nullptr, 0, 0, 0, 0, nullptr, nullptr, 0,
                                         0, nullptr, nullptr, desc);
   return cudaGetLastError();
 }

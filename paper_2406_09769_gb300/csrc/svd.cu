@@ -77,6 +77,9 @@ __device__ __forceinline__ float quad_sum(float v) {
 // positive (round-off of a semi-definite R) leaves column j of C zero and the
 // trailing block untouched.  Output in place of R_k: B[j][l] = C[l][j]
 // (row-major, upper triangular), the K-major second operand of K = M C.
+// kMode 0: strided batch; 1: grouped (CTA i factors problem desc[i]); 2: as 1
+// with the range guard checked on every global access.
+template <int kMode>
 __global__ void __launch_bounds__(kThreads, 2) k_chol_env(float* __restrict__ R, long long sR,
                                                           const int64_t* __restrict__ r_off,
                                                           const int32_t* __restrict__ D,
@@ -90,9 +93,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_chol_env(float* __restrict__ R,
   float* Rg;
   float am;
   const GuardTab* gd = nullptr;
-  if (desc) {  // grouped launch: CTA i factors problem desc[i]
+  if (kMode) {  // grouped launch: CTA i factors problem desc[i]
     const CholDesc d = desc[blockIdx.x];
-    gd = d.guard;
+    gd = kMode == 2 ? d.guard : nullptr;
     n = d.n;
     Rg = d.R;
     am = guard_ok(gd, d.amax, 4, 0x401) ? __uint_as_float(*d.amax) : 1.f;
@@ -301,8 +304,10 @@ __device__ __forceinline__ float half_sum(float v) {
   return v;
 }
 
-// desc != NULL: grouped launch, CTA i takes problem desc[i] (its own pointers and
-// shape; the strided arguments are ignored).
+// kMode 0: strided batch; 1: grouped launch, CTA i takes problem desc[i] (its
+// own pointers and shape; the strided arguments are ignored); 2: as 1 with the
+// range guard checked on every global access.
+template <int kMode>
 __global__ void __launch_bounds__(kThreads, 2) k_svd_left(const float* __restrict__ Kg_,
                                                            long long sK, int m_, int n_,
                                                            float* __restrict__ Ug_, long long sU,
@@ -312,8 +317,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_svd_left(const float* __restric
                                                            int* __restrict__ status_, int rounds,
                                                            const SvdDesc* __restrict__ desc) {
   extern __shared__ __align__(16) float sm[];
-  const SvdDesc* dq = desc ? desc + blockIdx.x : nullptr;
-  const GuardTab* gd = dq ? dq->guard : nullptr;
+  const SvdDesc* dq = kMode ? desc + blockIdx.x : nullptr;
+  const GuardTab* gd = kMode == 2 ? dq->guard : nullptr;
   const float* Kg = dq ? dq->K : Kg_;
   float* Ug = dq ? dq->U : Ug_;
   float* Utg = dq ? dq->Ut : Utg_;
@@ -917,13 +922,16 @@ cudaError_t launch_chol_env(float* R, long long sR, const int64_t* r_off, const 
                             int maxD, const unsigned int* amax, long long s_amax, int k0, int nk,
                             int batch, cudaStream_t st) {
   if (maxD < 1 || maxD > kNmax || nk < 1) return cudaErrorInvalidValue;
-  k_chol_env<<<batch * nk, kThreads, 0, st>>>(R, sR, r_off, D, amax, s_amax, k0, nk, nullptr);
+  k_chol_env<0><<<batch * nk, kThreads, 0, st>>>(R, sR, r_off, D, amax, s_amax, k0, nk, nullptr);
   return cudaGetLastError();
 }
 
-cudaError_t launch_chol_grouped(const CholDesc* desc, int n_prob, cudaStream_t st) {
+cudaError_t launch_chol_grouped(const CholDesc* desc, int n_prob, bool guarded, cudaStream_t st) {
   if (n_prob <= 0) return cudaSuccess;
-  k_chol_env<<<n_prob, kThreads, 0, st>>>(nullptr, 0, nullptr, nullptr, nullptr, 0, 0, 1, desc);
+  if (guarded)
+    k_chol_env<2><<<n_prob, kThreads, 0, st>>>(nullptr, 0, nullptr, nullptr, nullptr, 0, 0, 1, desc);
+  else
+    k_chol_env<1><<<n_prob, kThreads, 0, st>>>(nullptr, 0, nullptr, nullptr, nullptr, 0, 0, 1, desc);
   return cudaGetLastError();
 }
 
@@ -944,18 +952,19 @@ cudaError_t launch_svd_left(const float* K, long long sK, int m, int n, float* U
   if (!svd_left_supported(m, n, r) || nlam < 0 || nlam > m || rounds < 1 || rounds > 16)
     return cudaErrorInvalidValue;
   const size_t smem = svd_left_smem_bytes(m, n, r);
-  k_svd_left<<<batch, kThreads, smem, st>>>(K, sK, m, n, U, sU, Ut, sUt, lam, slam, r, nlam,
+  k_svd_left<0><<<batch, kThreads, smem, st>>>(K, sK, m, n, U, sU, Ut, sUt, lam, slam, r, nlam,
                                             status, rounds, nullptr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_svd_left_grouped(const SvdDesc* desc, int n_prob, int max_m, int max_n,
-                                    int max_r, cudaStream_t st, int rounds) {
+                                    int max_r, bool guarded, cudaStream_t st, int rounds) {
   if (n_prob <= 0) return cudaSuccess;
   if (!svd_left_supported(max_m, max_n, max_r) || rounds < 1 || rounds > 16)
     return cudaErrorInvalidValue;
   const size_t smem = svd_left_smem_bytes(max_m, max_n, max_r);
-  k_svd_left<<<n_prob, kThreads, smem, st>>>(nullptr, 0, 0, 0, nullptr, 0, nullptr, 0, nullptr, 0,
+  auto kern = guarded ? k_svd_left<2> : k_svd_left<1>;
+  kern<<<n_prob, kThreads, smem, st>>>(nullptr, 0, 0, 0, nullptr, 0, nullptr, 0, nullptr, 0,
                                              0, 0, nullptr, rounds, desc);
   return cudaGetLastError();
 }
@@ -968,8 +977,11 @@ cudaError_t svd_configure() {
   if (e != cudaSuccess) return e;
   const size_t need_svd = svd_left_smem_bytes(kNmax, kNmax, kRmax);
   if (need_svd > size_t(optin)) return cudaErrorInvalidValue;
-  return cudaFuncSetAttribute(k_svd_left, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(need_svd));
+  for (auto kern : {k_svd_left<0>, k_svd_left<1>, k_svd_left<2>}) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(need_svd));
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace tn
