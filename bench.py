@@ -61,6 +61,10 @@ def parse():
                    help="skip the cubic and random-regular workloads (N=1 only)")
     p.add_argument("--no-batched-arm", action="store_true",
                    help="skip the heterogeneous-batch measurement (N=1 only)")
+    p.add_argument("--paper-workloads", action="store_true",
+                   help="instead of the benchmark: the paper's Ising workloads (5x5x5 at "
+                        "beta 0.3, 28x28 at beta 0.44, random 3-regular graph of 220 vertices) "
+                        "over partition sizes and chi, FP64 and TF32, one JSON line")
     return p.parse_args()
 
 
@@ -733,8 +737,107 @@ def bench_ours(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------ the paper's Ising workloads
+
+PAPER_CHIS = (16, 32, 64)
+PAPER_SWAP = 32
+
+
+def _paper_cases():
+    """(name, workload, parts, swap batch) of the paper's Ising experiments
+    (Sec. "Impact of the environment size"): 5x5x5 lattice at beta 0.3 with parts
+    of 1, 3, 5 sites of a z-fibre; 28x28 lattice at beta 0.44 with parts of 14
+    sites and whole rows; a random 3-regular graph of 220 vertices (beta 0.3, the
+    batched workload's) with parts of 3 and 6 vertices along the
+    recursive-bisection order.  Swap batch 32 as in the paper, except parts of 6
+    on the random graph (swap batch 4: at 32 a block's intermediate exceeds the
+    gather programs' scratch)."""
+    from workloads import ising
+    w5 = ising.cubic(5, 5, 5, 0.3)
+    w28 = ising.lattice2d(28, 28, 0.44, "ferro")
+    wr = ising.random_regular(220, 3, 0.3, 220)
+    return [("cubic_5x5x5_beta0.3", w5, k, PAPER_SWAP) for k in (1, 3, 5)] + \
+           [("square_28x28_beta0.44", w28, k, PAPER_SWAP) for k in (14, 28)] + \
+           [("random_3_regular_220_beta0.3", wr, 3, PAPER_SWAP),
+            ("random_3_regular_220_beta0.3", wr, 6, 4)]
+
+
+_KAC_WARD_SNIPPET = r"""
+import json, sys
+sys.path.insert(0, {root!r})
+from oracle import exact
+from workloads import ising
+w = ising.lattice2d(28, 28, 0.44, "ferro")
+print(json.dumps(exact.ising_logz_kac_ward(28, 28, w["edges"], w["J"], w["beta"])))
+"""
+
+
+def paper_workloads(args):
+    """One contraction per (workload, parts, chi, precision), CUDA-event timed
+    (a warm-up call first on the mixed path); relative ln Z error against the exact Kac-Ward
+    value (28x28, computed in a CPU subprocess by the oracle) or, where no exact
+    value exists, against the FP64 run at the largest chi and partition."""
+    import torch
+    from paper_2406_09769_gb300 import binding as B
+    local = torch.device("cuda", 0)
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    ctx = B.tn_ctx_create(0)
+    rows = []
+    for name, w, k, swap in _paper_cases():
+        deg = np.full(len(w["edges"]), 2)
+        for chi in PAPER_CHIS:
+            plan = B.tn_plan(w["n"], w["edges"], deg, chi, env_size=k, swap_batch=swap)
+            info = B.tn_plan_query(plan)
+            buf = torch.from_numpy(B.pack_sites(plan, w["tensors"])).to(local)
+            row = {"workload": name, "sites_per_part": k, "swap_batch": swap, "chi": chi,
+                   "dm_passes": info["n_dm_passes"], "max_tree_edge": info["max_bond"],
+                   "planner": "general" if info["general"] else "boundary"}
+            for prec, pname in ((B.TN_PREC_FP64, "fp64"), (B.TN_PREC_TF32, "tf32")):
+                fn = lambda: B.tn_contract_approx(ctx, [plan], [buf.data_ptr()], prec, 0, sh)
+                if prec != B.TN_PREC_FP64:  # FP64 runs take seconds: no warm-up call
+                    fn()
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                lz, st = B.tn_logz(ctx, 1, raise_on_error=False)
+                row[pname] = {"ms": e0.elapsed_time(e1), "logz": float(lz[0]),
+                              "status": int(st[0])}
+            rows.append(row)
+    # references
+    exact28 = None
+    if not args.no_cpu_baseline:
+        code = _KAC_WARD_SNIPPET.format(root=ROOT)
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
+        if r.returncode == 0:
+            exact28 = float(json.loads(r.stdout.strip().splitlines()[-1]))
+    best = {}
+    for row in rows:
+        key = row["workload"]
+        cand = (row["chi"], row["sites_per_part"])
+        if key not in best or cand > best[key][0]:
+            best[key] = (cand, row["fp64"]["logz"])
+    for row in rows:
+        if row["workload"].startswith("square_28x28") and exact28 is not None:
+            ref, what = exact28, "exact (Kac-Ward)"
+        else:
+            ref, what = best[row["workload"]][1], "FP64 at the largest chi and partition"
+        row["reference"] = what
+        for pname in ("fp64", "tf32"):
+            row[pname]["rel_err"] = abs(row[pname]["logz"] - ref) / abs(ref)
+    print(json.dumps({"paper_workloads": rows, "data": "synthetic", "n_gpus": 1}), flush=True)
+
+
 def main():
     args = parse()
+    if args.paper_workloads:
+        paper_workloads(args)
+        return
     if args.impl == "reference":
         bench_reference(args)
     else:
