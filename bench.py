@@ -743,12 +743,20 @@ PAPER_CHIS = (16, 32, 64)
 PAPER_SWAP = 32
 
 
+def _fibre_parts(L, k):
+    """Part id per site of the open L^3 lattice (site (x * L + y) * L + z): every
+    z-fibre cut into portions of k consecutive sites (the last one shorter)."""
+    per = (L + k - 1) // k
+    return np.array([(v // L) * per + (v % L) // k for v in range(L ** 3)], dtype=np.int32)
+
+
 def _paper_cases():
     """(name, workload, parts, swap batch) of the paper's Ising experiments
     (Sec. "Impact of the environment size"): 5x5x5 lattice at beta 0.3 with parts
-    of 1, 3, 5 sites of a z-fibre; 28x28 lattice at beta 0.44 with parts of 14
-    sites and whole rows; a random 3-regular graph of 220 vertices (beta 0.3, the
-    batched workload's) with parts of 3 and 6 vertices along the
+    of 1, 3, 5 sites of a z-fibre (parts of 3: every fibre cut into portions of 3
+    and 2 sites, so no part spans two fibres); 28x28 lattice at beta 0.44 with
+    parts of 14 sites and whole rows; a random 3-regular graph of 220 vertices
+    (beta 0.3, the batched workload's) with parts of 3 and 6 vertices along the
     recursive-bisection order.  Swap batch 32 as in the paper, except parts of 6
     on the random graph (swap batch 4: at 32 a block's intermediate exceeds the
     gather programs' scratch)."""
@@ -756,7 +764,8 @@ def _paper_cases():
     w5 = ising.cubic(5, 5, 5, 0.3)
     w28 = ising.lattice2d(28, 28, 0.44, "ferro")
     wr = ising.random_regular(220, 3, 0.3, 220)
-    return [("cubic_5x5x5_beta0.3", w5, k, PAPER_SWAP) for k in (1, 3, 5)] + \
+    return [("cubic_5x5x5_beta0.3", w5, k, PAPER_SWAP) for k in (1, 5)] + \
+           [("cubic_5x5x5_beta0.3", w5, _fibre_parts(5, 3), PAPER_SWAP)] + \
            [("square_28x28_beta0.44", w28, k, PAPER_SWAP) for k in (14, 28)] + \
            [("random_3_regular_220_beta0.3", wr, 3, PAPER_SWAP),
             ("random_3_regular_220_beta0.3", wr, 6, 4)]
@@ -787,11 +796,16 @@ def paper_workloads(args):
     rows = []
     for name, w, k, swap in _paper_cases():
         deg = np.full(len(w["edges"]), 2)
+        part = None
+        if not np.isscalar(k):  # an explicit partition (fibre portions)
+            part, k = k, int(np.bincount(k).max())
         for chi in PAPER_CHIS:
-            plan = B.tn_plan(w["n"], w["edges"], deg, chi, env_size=k, swap_batch=swap)
+            plan = B.tn_plan(w["n"], w["edges"], deg, chi, env_size=0 if part is not None else k,
+                             partition=part, swap_batch=swap)
             info = B.tn_plan_query(plan)
             buf = torch.from_numpy(B.pack_sites(plan, w["tensors"])).to(local)
             row = {"workload": name, "sites_per_part": k, "swap_batch": swap, "chi": chi,
+                   "parts": "fibre portions" if part is not None else "consecutive ids",
                    "dm_passes": info["n_dm_passes"], "max_tree_edge": info["max_bond"],
                    "planner": "general" if info["general"] else "boundary"}
             for prec, pname in ((B.TN_PREC_FP64, "fp64"), (B.TN_PREC_TF32, "tf32")):
