@@ -130,6 +130,7 @@ struct tn_ctx {
   std::vector<cudaStream_t> pool;
   std::vector<cudaEvent_t> joins;
   cudaEvent_t fork = nullptr;
+  cudaEvent_t gready = nullptr;  // grouped batches: tables and site norms done
 };
 
 namespace {
@@ -1025,6 +1026,7 @@ struct GLaunch {
   int count;
   int64_t p0, p1, p2;  // launch extents (max elements / max M, N / max m, n, r);
                        // close: bucket, step
+  int grp = 0;         // bucket group (stream) of the launch
 };
 
 struct GBuild {
@@ -1276,14 +1278,65 @@ void merge_grouped(const std::vector<std::vector<GOp1>>& per, GBuild& gb) {
   }
 }
 
-// Builds the launch list of a grouped batch (see above).
-void build_grouped(tn_ctx* c, const std::vector<Bucket>& bks, const std::vector<WsF>& ws,
-                   bool factored, double* res_logscale, int* res_status, GBuild& gb,
+// Splits the buckets into n_groups groups of similar path length and matrix
+// sizes (each group runs its own lockstep sequence on a stream of its own, so
+// small instances neither wait for the largest ones' vertex loops nor ride in
+// launches timed by their matrices): buckets sorted by a cost proxy (per tree
+// vertex of every pass, 0.2 + (min(A_v, D_v) / 128)^1.5, the eigenvector
+// problem's size) and cut into contiguous runs of equal count.
+std::vector<std::vector<size_t>> group_buckets(const std::vector<Bucket>& bks, size_t n_groups) {
+  std::vector<std::pair<double, size_t>> cost;
+  for (size_t b = 0; b < bks.size(); ++b) {
+    double w = 0.0;
+    for (const tn::Step& st : bks[b].P->steps)
+      if (st.kind == 1)
+        for (int k = 1; k <= st.n - 2; ++k) {
+          const double p = std::min(st.r[k - 1] * st.d[k], st.D[k]);
+          w += 0.2 + std::pow(p / 128.0, 1.5);
+        }
+    cost.push_back({w, b});
+  }
+  std::stable_sort(cost.begin(), cost.end(),
+                   [](const std::pair<double, size_t>& a, const std::pair<double, size_t>& b) {
+                     return a.first > b.first;
+                   });
+  const size_t G = std::max<size_t>(1, std::min(n_groups, bks.size()));
+  std::vector<std::vector<size_t>> groups(G);
+  for (size_t i = 0; i < cost.size(); ++i) groups[i * G / cost.size()].push_back(cost[i].second);
+  return groups;
+}
+
+// Builds the launch list of a grouped batch (see above): every group's
+// lockstep list, the groups' launches interleaved round robin (so that the
+// host issues all streams' work evenly).
+void build_grouped(const std::vector<Bucket>& bks, const std::vector<WsF>& ws,
+                   const std::vector<std::vector<size_t>>& groups, bool factored,
+                   double* res_logscale, int* res_status, GBuild& gb,
                    const tn::GuardTab* guard = nullptr) {
-  std::vector<std::vector<GOp1>> per;
-  for (size_t b = 0; b < bks.size(); ++b)
-    per.push_back(bucket_ops(bks, b, ws[b], factored, res_logscale, res_status, guard));
-  merge_grouped(per, gb);
+  std::vector<GBuild> per_group(groups.size());
+  for (size_t g = 0; g < groups.size(); ++g) {
+    std::vector<std::vector<GOp1>> per;
+    for (size_t b : groups[g])
+      per.push_back(bucket_ops(bks, b, ws[b], factored, res_logscale, res_status, guard));
+    merge_grouped(per, per_group[g]);
+  }
+  std::vector<size_t> base(groups.size(), 0), next(groups.size(), 0);
+  for (size_t g = 0; g < groups.size(); ++g) {
+    base[g] = (gb.bytes.size() + 255) & ~size_t(255);
+    gb.bytes.resize(base[g]);
+    gb.bytes.insert(gb.bytes.end(), per_group[g].bytes.begin(), per_group[g].bytes.end());
+  }
+  for (bool more = true; more;) {
+    more = false;
+    for (size_t g = 0; g < groups.size(); ++g) {
+      if (next[g] >= per_group[g].launches.size()) continue;
+      GLaunch L = per_group[g].launches[next[g]++];
+      if (L.kind != 8) L.off += base[g];
+      L.grp = int(g);
+      gb.launches.push_back(L);
+      more = true;
+    }
+  }
 }
 
 // Host-side range check of a grouped launch list (TN_GROUPED_CHECK=1): every
@@ -1423,8 +1476,14 @@ void run_grouped_tc(tn_ctx* c, const std::vector<Bucket>& bks, bool factored, bo
     gdev = reinterpret_cast<tn::GuardTab*>(gbase);
     grec = t.rec;
   }
+  // bucket groups on the pool streams (one group on strm in guard mode)
+  const bool multi = !guard_mode && !c->pool.empty() && bks.size() >= 8;
+  const size_t n_groups = multi ? std::min<size_t>(c->pool.size(), bks.size() / 4) : 1;
+  std::vector<cudaStream_t> gs;
+  for (size_t g = 0; g < n_groups; ++g) gs.push_back(multi ? c->pool[g] : strm);
   GBuild gb;
-  build_grouped(c, bks, ws, factored, res_logscale, res_status, gb, gdev);
+  build_grouped(bks, ws, group_buckets(bks, n_groups), factored, res_logscale, res_status, gb,
+                gdev);
   if (const char* e = std::getenv("TN_GROUPED_CHECK"))
     if (e[0] == '1') {
       check_grouped(bks, gb);
@@ -1447,6 +1506,12 @@ void run_grouped_tc(tn_ctx* c, const std::vector<Bucket>& bks, bool factored, bo
   if (upload && !gb.bytes.empty())
     ck(cudaMemcpyAsync(dbase, gb.bytes.data(), gb.bytes.size(), cudaMemcpyHostToDevice, strm),
        "upload grouped tables");
+  if (multi) {  // every group stream starts after the tables and the site norms
+    if (!c->gready) ck(cudaEventCreateWithFlags(&c->gready, cudaEventDisableTiming),
+                       "cudaEventCreate");
+    ck(cudaEventRecord(c->gready, strm), "cudaEventRecord");
+    for (cudaStream_t q : gs) ck(cudaStreamWaitEvent(q, c->gready, 0), "cudaStreamWaitEvent");
+  }
   if (guard_mode && !gb.bytes.empty()) {
     std::vector<char> back(gb.bytes.size());
     ck(cudaStreamSynchronize(strm), "guard: sync");
@@ -1485,6 +1550,7 @@ void run_grouped_tc(tn_ctx* c, const std::vector<Bucket>& bks, bool factored, bo
   for (size_t li = 0; li < gb.launches.size(); ++li) {
     const GLaunch& g = gb.launches[li];
     char* d = dbase + g.off;
+    cudaStream_t ls = gs[size_t(g.grp)];
     if (guard_mode && launch_bytes(g)) {
       // this launch's descriptors are still as uploaded
       std::vector<char> back(launch_bytes(g));
@@ -1498,44 +1564,44 @@ void run_grouped_tc(tn_ctx* c, const std::vector<Bucket>& bks, bool factored, bo
     }
     switch (g.kind) {
       case 0:
-        Scope(c, g.cls, strm),
+        Scope(c, g.cls, ls),
         ck(tn::launch_gather_grouped(reinterpret_cast<tn::GatherDesc*>(d), g.count, g.p0, guard_mode,
-                                     strm),
+                                     ls),
            "grouped gather");
         break;
       case 1:
-        Scope(c, g.cls, strm),
-        ck(tn::launch_env_root_grouped(reinterpret_cast<tn::EnvRootDesc*>(d), g.count, strm),
+        Scope(c, g.cls, ls),
+        ck(tn::launch_env_root_grouped(reinterpret_cast<tn::EnvRootDesc*>(d), g.count, ls),
            "grouped env root");
         break;
       case 2:
       case 3:
-        Scope(c, g.cls, strm),
+        Scope(c, g.cls, ls),
         ck(tn::launch_gemm_grouped(reinterpret_cast<tn::GemmDesc*>(d), g.count, int(g.p0),
-                                   int(g.p1), g.kind == 3 && c->value_comp, guard_mode, strm),
+                                   int(g.p1), g.kind == 3 && c->value_comp, guard_mode, ls),
            "grouped gemm");
         break;
       case 4:
-        Scope(c, g.cls, strm),
-        ck(tn::launch_chol_grouped(reinterpret_cast<tn::CholDesc*>(d), g.count, guard_mode, strm),
+        Scope(c, g.cls, ls),
+        ck(tn::launch_chol_grouped(reinterpret_cast<tn::CholDesc*>(d), g.count, guard_mode, ls),
            "grouped cholesky");
         break;
       case 5:
-        Scope(c, g.cls, strm),
+        Scope(c, g.cls, ls),
         ck(tn::launch_svd_left_grouped(reinterpret_cast<tn::SvdDesc*>(d), g.count, int(g.p0),
-                                       int(g.p1), int(g.p2), guard_mode, strm, c->eig_rounds),
+                                       int(g.p1), int(g.p2), guard_mode, ls, c->eig_rounds),
            "grouped svd");
         break;
       case 6:
-        Scope(c, g.cls, strm),
+        Scope(c, g.cls, ls),
         ck(tn::launch_eigh_grouped(reinterpret_cast<tn::EighDesc*>(d), g.count, int(g.p0),
-                                   int(g.p1), guard_mode, strm),
+                                   int(g.p1), guard_mode, ls),
            "grouped eigh");
         break;
       case 7:
-        Scope(c, g.cls, strm),
+        Scope(c, g.cls, ls),
         ck(tn::launch_root_grouped(reinterpret_cast<tn::RootDesc*>(d), g.count, int(g.p0), guard_mode,
-                                   strm),
+                                   ls),
            "grouped root");
         break;
       case 8: {
@@ -1543,11 +1609,11 @@ void run_grouped_tc(tn_ctx* c, const std::vector<Bucket>& bks, bool factored, bo
         const tn::Step& st = bk.P->steps[size_t(g.p1)];
         int maxD = 1;
         for (int k = 0; k < st.n; ++k) maxD = std::max(maxD, st.D[k]);
-        Scope(c, TN_KC_CLOSE, strm),
+        Scope(c, TN_KC_CLOSE, ls),
         ck(tn::launch_close_f32(ws[size_t(g.p0)].Y, ws[size_t(g.p0)].sY,
                                 bk.tabs[size_t(g.p1)].y_off, bk.tabs[size_t(g.p1)].D, st.n, maxD,
                                 res_logscale + bk.res_off, res_logz + bk.res_off,
-                                res_status + bk.res_off, int(bk.idx.size()), strm),
+                                res_status + bk.res_off, int(bk.idx.size()), ls),
            "close");
         break;
       }
@@ -1805,6 +1871,7 @@ extern "C" tn_status tn_ctx_destroy(tn_ctx_t* c) {
   for (cudaStream_t ps : c->pool) cudaStreamDestroy(ps);
   for (cudaEvent_t ev : c->joins) cudaEventDestroy(ev);
   if (c->fork) cudaEventDestroy(c->fork);
+  if (c->gready) cudaEventDestroy(c->gready);
   delete c;
   return TN_OK;
 }
