@@ -1278,12 +1278,15 @@ void merge_grouped(const std::vector<std::vector<GOp1>>& per, GBuild& gb) {
   }
 }
 
-// Splits the buckets into n_groups groups of similar path length and matrix
-// sizes (each group runs its own lockstep sequence on a stream of its own, so
-// small instances neither wait for the largest ones' vertex loops nor ride in
-// launches timed by their matrices): buckets sorted by a cost proxy (per tree
-// vertex of every pass, 0.2 + (min(A_v, D_v) / 128)^1.5, the eigenvector
-// problem's size) and cut into contiguous runs of equal count.
+// Splits the buckets into at most n_groups groups, each run as its own
+// lockstep sequence on a stream of its own: buckets sorted by a cost proxy (per
+// tree vertex of every pass, 0.2 + (min(A_v, D_v) / 128)^1.5, the eigenvector
+// problem's size), then groups of 1, 1, 2, 4, 8, ... buckets from the most
+// expensive down, the last group taking the rest.  The batch lasts as long as
+// its slowest group, and a group's lockstep sequence is at least its most
+// expensive member's path, stretched by every position where another member
+// has more vertices or larger matrices: the few most expensive instances get
+// groups of their own, the many cheap ones share.
 std::vector<std::vector<size_t>> group_buckets(const std::vector<Bucket>& bks, size_t n_groups) {
   std::vector<std::pair<double, size_t>> cost;
   for (size_t b = 0; b < bks.size(); ++b) {
@@ -1300,9 +1303,16 @@ std::vector<std::vector<size_t>> group_buckets(const std::vector<Bucket>& bks, s
                    [](const std::pair<double, size_t>& a, const std::pair<double, size_t>& b) {
                      return a.first > b.first;
                    });
-  const size_t G = std::max<size_t>(1, std::min(n_groups, bks.size()));
-  std::vector<std::vector<size_t>> groups(G);
-  for (size_t i = 0; i < cost.size(); ++i) groups[i * G / cost.size()].push_back(cost[i].second);
+  std::vector<std::vector<size_t>> groups;
+  size_t i = 0, size = 1;
+  while (i < cost.size()) {
+    const bool last = groups.size() + 1 >= std::max<size_t>(1, n_groups);
+    const size_t take = last ? cost.size() - i : std::min(size, cost.size() - i);
+    groups.emplace_back();
+    for (size_t j = 0; j < take; ++j) groups.back().push_back(cost[i + j].second);
+    i += take;
+    if (groups.size() >= 2) size *= 2;
+  }
   return groups;
 }
 
@@ -1478,12 +1488,12 @@ void run_grouped_tc(tn_ctx* c, const std::vector<Bucket>& bks, bool factored, bo
   }
   // bucket groups on the pool streams (one group on strm in guard mode)
   const bool multi = !guard_mode && !c->pool.empty() && bks.size() >= 8;
-  const size_t n_groups = multi ? std::min<size_t>(c->pool.size(), bks.size() / 4) : 1;
+  const std::vector<std::vector<size_t>> groups =
+      group_buckets(bks, multi ? c->pool.size() : 1);
   std::vector<cudaStream_t> gs;
-  for (size_t g = 0; g < n_groups; ++g) gs.push_back(multi ? c->pool[g] : strm);
+  for (size_t g = 0; g < groups.size(); ++g) gs.push_back(multi ? c->pool[g] : strm);
   GBuild gb;
-  build_grouped(bks, ws, group_buckets(bks, n_groups), factored, res_logscale, res_status, gb,
-                gdev);
+  build_grouped(bks, ws, groups, factored, res_logscale, res_status, gb, gdev);
   if (const char* e = std::getenv("TN_GROUPED_CHECK"))
     if (e[0] == '1') {
       check_grouped(bks, gb);
