@@ -439,6 +439,16 @@ enum {
  *     step, pass section, tree vertex).  1 (default): on; 0: one launch
  *     sequence per bucket on a pool of streams.                             */
 enum { TN_OPT_EIG_ROUNDS = 1, TN_OPT_WAIT_PROBE = 2, TN_OPT_VALUE_PATH = 3, TN_OPT_GROUPED = 4 };
+/* Diagnostics read from the environment (none changes a result):
+ *   TN_FAULT_ALLOC_AT=n  the n-th device allocation of the process fails
+ *                        without a CUDA call (TN_ERR_OOM), for failure tests;
+ *   TN_GROUPED_CHECK=1   a grouped batch checks every descriptor's operand
+ *                        ranges on the host and launches nothing (the call
+ *                        returns TN_ERR_INVALID with a summary);
+ *   TN_GROUPED_GUARD=1   a grouped batch runs on one stream with every global
+ *                        access checked against the batch's allocations, a
+ *                        synchronisation after each launch, and the first
+ *                        access outside them reported (TN_ERR_INVALID).      */
 tn_status tn_ctx_set_option(tn_ctx_t* ctx, int32_t option, int64_t value);
 
 /* Turn per-launch CUDA-event timing on (1) or off (0) for later batches of
