@@ -61,6 +61,8 @@ def parse():
                    help="skip the cubic and random-regular workloads (N=1 only)")
     p.add_argument("--no-batched-arm", action="store_true",
                    help="skip the heterogeneous-batch measurement (N=1 only)")
+    p.add_argument("--rrg-batch", type=int, default=256,
+                   help="instances of the random 3-regular arm (the workload's batch is 256)")
     p.add_argument("--paper-workloads", action="store_true",
                    help="instead of the benchmark: the paper's Ising workloads (5x5x5 at "
                         "beta 0.3, 28x28 at beta 0.44, random 3-regular graph of 220 vertices) "
@@ -286,14 +288,15 @@ def _timed_call(torch, stream, flush, fn):
     return e0.elapsed_time(e1)
 
 
-def general_arms(B, torch, local, stream, flush):
+def general_arms(B, torch, local, stream, flush, n_rrg=RRG_BATCH):
     """Workloads of the general planner.
 
     cubic: the open 6x6x6 Ising ferromagnet at beta in CUBIC_BETAS (one batch
     of three instances sharing a plan), parts of k consecutive sites of a
     z-fibre, chi per CUBIC_RUNS, FP64 and TF32.
-    rrg: the RRG_BATCH instances of the batched random 3-regular workload
-    (n in [40, 200], J = +-1, beta 0.3, chi per instance in {16, 32, 48, 64}),
+    rrg: the first n_rrg (default RRG_BATCH, all) instances of the batched
+    random 3-regular workload (n in [40, 200], J = +-1, beta 0.3, chi per
+    instance in {16, 32, 48, 64}),
     parts of RRG_PARTS vertices along the recursive-bisection order, swap batch
     RRG_SWAP, in one call: TF32 on the grouped executor (every operation one
     launch over all instances) eager and as a captured graph, FP64 on the first
@@ -317,7 +320,7 @@ def general_arms(B, torch, local, stream, flush):
             row[name] = {"ms": ms, "value": 3 / (ms / 1e3), "logz": [float(x) for x in lz],
                          "status_ok": int((st == 0).sum())}
         cubic.append(row)
-    rws = [ising.config4_instance(i) for i in range(RRG_BATCH)]
+    rws = [ising.config4_instance(i) for i in range(n_rrg)]
     plans = [B.tn_plan(w["n"], w["edges"], np.full(len(w["edges"]), 2), w["chi"],
                        env_size=RRG_PARTS, swap_batch=RRG_SWAP) for w in rws]
     infos = [B.tn_plan_query(p) for p in plans]
@@ -336,7 +339,7 @@ def general_arms(B, torch, local, stream, flush):
                         lambda: B.tn_contract_approx(ctx, plans[:nf], ptrs[:nf], B.TN_PREC_FP64,
                                                      0, sh))
     lz_64, st_64 = B.tn_logz(ctx, nf, raise_on_error=False)
-    rrg = {"workload": f"{RRG_BATCH} random 3-regular graphs "
+    rrg = {"workload": f"{n_rrg} random 3-regular graphs "
                        "(n in [40, 200], J = +-1, beta 0.3, chi in {16, 32, 48, 64} per "
                        f"instance, seeded); parts of {RRG_PARTS} vertices, swap batch {RRG_SWAP}",
            "executor": "grouped: the instances advance in lockstep, every operation one "
@@ -680,7 +683,7 @@ def bench_ours(args):
         hetero = batched_arm(B, torch, dev, stream, flush)
     gen = None
     if world == 1 and not args.no_general_arms:
-        gen = general_arms(B, torch, dev, stream, flush)
+        gen = general_arms(B, torch, dev, stream, flush, args.rrg_batch)
 
     out = {
         "metric": "approx contractions/s", "value": value, "unit": "contractions/s",
