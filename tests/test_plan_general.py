@@ -91,3 +91,31 @@ def test_oversized_cut_is_rejected():
     with pytest.raises(B.TNError) as e:
         _lib_steps(w, 12, 64, 0)
     assert e.value.status == 8
+
+
+def test_explicit_partition_fibre_portions_equals_oracle():
+    """An explicit partition (the 5x5x5 lattice with every z-fibre cut into
+    portions of 3 and 2 sites, as the paper's parts of 3 on that lattice): no
+    part spans two fibres, and the library's plan equals the oracle's."""
+    import bench
+    w = ising.cubic(5, 5, 5, 0.3)
+    part = bench._fibre_parts(5, 3)
+    parts = [list(np.where(part == p)[0]) for p in range(part.max() + 1)]
+    for vs in parts:
+        assert len({v // 5 for v in vs}) == 1 and len(vs) in (2, 3)
+    P = general.plan(w["n"], w["edges"], [2] * len(w["edges"]), parts, 16, 32)
+    ref = []
+    for st in P["steps"]:
+        if st["close"]:
+            ref.append(dict(kind=2, D=st["D"]))
+        else:
+            for p in st["passes"]:
+                ref.append(dict(kind=1, leaves=[l[1] for l in p["leaves"]], D=p["D"], r=p["r"]))
+    plan = B.tn_plan(w["n"], w["edges"], np.full(len(w["edges"]), 2), 16, env_size=0,
+                     partition=part, swap_batch=32)
+    got = B.tn_plan_steps(plan)
+    assert len(got) == len(ref)
+    for a, b in zip(ref, got):
+        assert a["kind"] == b["kind"] and a["D"] == b["D"]
+        if a["kind"] == 1:
+            assert a["leaves"] == b["leaves"] and a["r"] == b["r"]
