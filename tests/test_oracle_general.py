@@ -2,8 +2,9 @@
 and the mathematics fix, independent of the oracle's own arithmetic:
 
   * chi at or above every cut rank reproduces the exact ln Z (brute-force spin
-    sums) on random regular graphs and 3D lattices, with
-    and without swap passes (Algorithm approx_tensor_network);
+    sums) on random regular graphs and 3D lattices (parts of consecutive ids
+    and explicit partitions into fibre portions), with and without swap passes
+    (Algorithm approx_tensor_network);
   * on 2D lattices with rows as parts the general plan reproduces the row
     oracle at truncating chi: the tree and the leaf order are the same and
     Def. "density matrix" makes the result independent of the embedding phi;
@@ -41,6 +42,22 @@ def test_exact_at_full_rank_cubic(shape, env):
     w = ising.cubic(*shape, 0.25)
     ex = exact.ising_logz_bruteforce(w["n"], w["edges"], w["J"], w["beta"])
     R = general.partitioned_contract_graph(w, general.parts_from_env(w["n"], env), 1 << 10)
+    assert _rel(R["logz"], ex) < 1e-12
+
+
+@pytest.mark.parametrize("shape,portion", [((2, 3, 3), 2), ((3, 2, 3), 2), ((2, 2, 5), 3)])
+def test_exact_at_full_rank_fibre_portions(shape, portion):
+    """An explicit partition that is not runs of consecutive ids in a
+    different order: every z-fibre cut into portions (the last one shorter),
+    swap passes on; chi above every cut rank reproduces the brute-force sum."""
+    Lx, Ly, Lz = shape
+    w = ising.cubic(Lx, Ly, Lz, 0.25)
+    per = (Lz + portion - 1) // portion
+    pid = [(v // Lz) * per + (v % Lz) // portion for v in range(w["n"])]
+    parts = [[v for v in range(w["n"]) if pid[v] == p] for p in range(max(pid) + 1)]
+    assert all(len({v // Lz for v in q}) == 1 for q in parts)
+    ex = exact.ising_logz_bruteforce(w["n"], w["edges"], w["J"], w["beta"])
+    R = general.partitioned_contract_graph(w, parts, 1 << 10, 1)
     assert _rel(R["logz"], ex) < 1e-12
 
 
